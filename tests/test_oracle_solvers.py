@@ -1,0 +1,192 @@
+"""Pins of the oracle's solvers and of the Dirichlet block operator A_s."""
+import numpy as np
+import pytest
+
+from oracle import dwf_operator as op
+from oracle import solvers as sv
+from paper_1811_08488_gb300 import synthetic as syn
+
+RNG = np.random.default_rng(3)
+MOB = dict(M5=1.8, b=1.5, c=0.5)
+
+
+def rand_even(act):
+    psi = RNG.normal(size=act.shape5) + 1j * RNG.normal(size=act.shape5)
+    return op.restrict_parity(psi, 0)
+
+
+def gauge(act, eps=0.4, seed=12):
+    return op.gauge_to_mu_major(syn.gauge_field(act.dims, eps, seed))
+
+
+def dense_on(fn, act, mask4):
+    """Dense matrix of fn on the even sites of mask4 (all s, spin, colour)."""
+    even = (op.parity_mask(act.shape4) == 0) & mask4
+    m5 = np.broadcast_to(even[None, :, :, :, :, None, None], act.shape5).reshape(-1)
+    idx = np.flatnonzero(m5)
+    n = m5.size
+    cols = []
+    for j in idx:
+        e = np.zeros(n, dtype=complex)
+        e[j] = 1
+        cols.append(fn(e.reshape(act.shape5)).reshape(-1)[idx])
+    return np.array(cols).T, idx
+
+
+# ----------------------------------------------------------------------------
+# CG against dense LU
+# ----------------------------------------------------------------------------
+def test_cg_matches_dense_solve():
+    act = op.Action(dims=(2, 2, 2, 2), Ls=4, **MOB)
+    U = gauge(act, eps=0.5)
+    mf = 0.1
+    A, idx = dense_on(lambda v: op.mdagm(act, U, v, mf), act, np.ones(act.shape4, bool))
+    b = rand_even(act)
+    x, it, res = sv.cg(lambda v: op.mdagm(act, U, v, mf), b, 1e-13)
+    assert res <= 1e-13
+    xd = np.linalg.solve(A, b.reshape(-1)[idx])
+    assert np.abs(x.reshape(-1)[idx] - xd).max() < 1e-10 * np.abs(xd).max()
+
+
+# ----------------------------------------------------------------------------
+# A_s: definition, box form, Hermiticity, snake terms
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,block", [
+    ((8, 4, 6, 4), (2, 2, 2, 4)),   # x: box 6 < L; y: L = b + 2; z: L = b + 4; t: one block
+    ((4, 8, 4, 8), (4, 2, 2, 4)),   # x: one block; y: box 6 < L; t: box = L
+])
+def test_block_operator_box_equals_definition(dims, block):
+    act = op.Action(dims=dims, Ls=3, **MOB)
+    U = gauge(act)
+    mf = 0.05
+    origins = sv.block_origins(act.dims, block)
+    for origin in [origins[0], origins[len(origins) // 2], origins[-1]]:
+        mask = sv.block_mask(act, block, origin)
+        x = sv.project(rand_even(act), mask)
+        want = sv.a_block(act, U, x, mf, mask)
+        got = sv.a_block_box(act, U, x, mf, origin, block)
+        assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+def test_block_operator_hermitian_pd_and_snake_terms():
+    act = op.Action(dims=(4, 4, 2, 4), Ls=4, **MOB)
+    U = gauge(act)
+    mf = 0.05
+    block = (2, 2, 2, 2)
+    origin = (2, 0, 0, 2)
+    mask = sv.block_mask(act, block, origin)
+    As, idx = dense_on(lambda v: sv.a_block(act, U, v, mf, mask), act, mask)
+    assert np.abs(As - As.conj().T).max() < 1e-13 * np.abs(As).max()
+    assert np.linalg.eigvalsh(As).min() > 0
+    # the snake terms are O(1): the truncated operator differs
+    At, _ = dense_on(lambda v: sv.a_block_truncated(act, U, v, mf, mask), act, mask)
+    assert np.abs(As - At).max() > 0.05 * np.abs(As).max()
+    assert np.abs(At - At.conj().T).max() < 1e-13 * np.abs(At).max()
+
+
+def test_single_block_is_whole_operator():
+    act = op.Action(dims=(4, 2, 2, 4), Ls=3, **MOB)
+    U = gauge(act)
+    mf = 0.05
+    mask = sv.block_mask(act, act.dims, (0, 0, 0, 0))
+    x = rand_even(act)
+    A = op.mdagm(act, U, x, mf)
+    assert np.abs(sv.a_block(act, U, x, mf, mask) - A).max() < 1e-13 * np.abs(A).max()
+    assert np.abs(sv.a_block_box(act, U, x, mf, (0, 0, 0, 0), act.dims) - A).max() < 1e-13 * np.abs(A).max()
+
+
+# ----------------------------------------------------------------------------
+# fixed-k inner CG
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small_block():
+    act = op.Action(dims=(4, 4, 4, 4), Ls=4, **MOB)
+    U = gauge(act, seed=5)
+    mf = 0.05
+    block = (2, 2, 2, 2)
+    origin = (0, 2, 2, 0)
+    mask = sv.block_mask(act, block, origin)
+    Aop = lambda v: sv.a_block(act, U, v, mf, mask)
+    As, idx = dense_on(Aop, act, mask)
+    r = sv.project(rand_even(act), mask)
+    return act, Aop, As, idx, r
+
+
+def test_inner_cg_k1_closed_form(small_block):
+    act, Aop, As, idx, r = small_block
+    z = sv.cg_fixed(Aop, r, 1)
+    want = op.norm2(r) / op.vdot(r, Aop(r)).real * r
+    assert np.abs(z - want).max() < 1e-14 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("k", [2, 3, 5])
+def test_inner_cg_is_krylov_optimal(small_block, k):
+    """CG_k minimises the A-norm error over the Krylov space K_k(A_s, r)."""
+    act, Aop, As, idx, r = small_block
+    rv = r.reshape(-1)[idx]
+    V = [rv]
+    for _ in range(k - 1):
+        V.append(As @ V[-1])
+    Q, _ = np.linalg.qr(np.array(V).T)
+    c = np.linalg.solve(Q.conj().T @ As @ Q, Q.conj().T @ rv)
+    want = Q @ c
+    z = sv.cg_fixed(Aop, r, k).reshape(-1)[idx]
+    assert np.abs(z - want).max() < 1e-9 * np.abs(want).max()
+
+
+def test_inner_cg_many_iterations_is_exact(small_block):
+    act, Aop, As, idx, r = small_block
+    z = sv.cg_fixed(Aop, r, 120).reshape(-1)[idx]
+    want = np.linalg.solve(As, r.reshape(-1)[idx])
+    assert np.abs(z - want).max() < 1e-10 * np.abs(want).max()
+
+
+# ----------------------------------------------------------------------------
+# MSPCG (Algorithm 1 with the multisplitting preconditioner)
+# ----------------------------------------------------------------------------
+def test_mspcg_solves_and_matches_dense():
+    act = op.Action(dims=(4, 2, 2, 4), Ls=4, **MOB)
+    U = gauge(act, eps=0.5, seed=8)
+    mf = 0.05
+    b = rand_even(act)
+    x, it, res = sv.mspcg(act, U, b, mf, (2, 2, 2, 2), 4, 1e-10)
+    assert res <= 1e-10
+    A, idx = dense_on(lambda v: op.mdagm(act, U, v, mf), act, np.ones(act.shape4, bool))
+    xd = np.linalg.solve(A, b.reshape(-1)[idx])
+    cond = np.linalg.cond(A)
+    assert np.abs(x.reshape(-1)[idx] - xd).max() <= 10 * cond * 1e-10 * np.abs(xd).max()
+    xc, itc, _ = sv.cg(lambda v: op.mdagm(act, U, v, mf), b, 1e-10)
+    assert it < itc
+
+
+def test_mspcg_one_block_large_k_converges_at_once():
+    act = op.Action(dims=(2, 2, 2, 4), Ls=4, **MOB)
+    U = gauge(act, eps=0.5, seed=9)
+    mf = 0.1
+    b = rand_even(act)
+    x, it, res = sv.mspcg(act, U, b, mf, act.dims, 150, 1e-10)
+    assert res <= 1e-10
+    assert it <= 2
+
+
+@pytest.mark.slow
+def test_table1_trends_on_synthetic_field():
+    """Trends of the paper's Table 1 (Sec. 3): MSPCG needs fewer outer
+    iterations than plain CG, more inner iterations help with diminishing
+    returns, and keeping the snake terms matters (Sec. 2.3)."""
+    act = op.Action(dims=(4, 4, 4, 8), Ls=4, **MOB)
+    U = gauge(act, eps=0.45, seed=13)
+    mf = 0.01
+    b = rand_even(act)
+    block = (4, 4, 4, 4)
+    tol = 1e-6
+    A = lambda v: op.mdagm(act, U, v, mf)
+    _, plain, _ = sv.cg(A, b, tol)
+    its = {}
+    for k in (2, 4, 8):
+        _, its[k], res = sv.mspcg(act, U, b, mf, block, k, tol)
+        assert res <= tol
+    assert its[2] < plain
+    assert its[2] >= its[4] >= its[8]
+    _, trunc, _ = sv.mspcg(act, U, b, mf, block, 4, tol, snake=False)
+    assert its[4] < trunc
