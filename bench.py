@@ -1,0 +1,341 @@
+"""Benchmark: MSPCG vs plain CG time-to-solve at residual 1e-10 on one GB300,
+and the hop (Dslash) kernel's HBM bandwidth.
+
+Workload (default): Moebius DWF 16^3 x 32 x Ls=12, b=1.5, c=0.5, M5=1.8,
+m_f=0.01, SU(3) links exp(i 0.4 H) (seed 1001), one Gaussian source (seed
+2001 + rank). MSPCG: 8^3 x 16 blocks (16 blocks), 6 inner CG iterations in
+FP16 storage, FP32 outer iterations with FP64 reductions and reliable updates.
+Plain CG: the same outer solver without the preconditioner.
+
+A step is one full MSPCG solve (every stage of the path) to a true residual
+of 1e-10. `value` is the mean MSPCG time-to-solution over the timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+and source; the timed region is bracketed by barriers and the maximum over
+ranks is reported ("replicas only": the path has no data exchange on one GPU).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (see cpu_sample()).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MSPCG vs plain CG time-to-solve at resid 1e-10 (1 GB300); Dslash HBM GB/s"
+WORKLOAD = "mobius_16^3x32x12"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["unsampled"]}
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+def cpu_sample(outer_iters, k, nblocks):
+    """Time one application of the oracle's block operator A_s on one
+    8^3 x 16 block of the workload (the cut-out box form, FP64 numpy) and
+    scale it to a full MSPCG solve: the oracle's cost is proportional to the
+    sites it sweeps, so A on the whole lattice costs t_As * V / V_box, and
+    one outer iteration costs A + k * nblocks * A_s."""
+    from oracle import dwf_operator as op
+    from oracle import solvers as sv
+    from paper_1811_08488_gb300 import synthetic as syn
+    w = syn.WORKLOADS[WORKLOAD]
+    act = op.Action(dims=w["dims"], Ls=w["Ls"], M5=w["M5"], b=w["b"], c=w["c"])
+    U = op.gauge_to_mu_major(syn.gauge_field(w["dims"], w["eps"], 1000 + w["id"]))
+    b = op.half_to_full(syn.half_field(w["dims"], w["Ls"], 2000 + w["id"]), 0)
+    block, origin = w["block"], (0, 0, 0, 0)
+    mask = sv.block_mask(act, block, origin)
+    t0 = time.perf_counter()
+    sv.a_block_box(act, U, sv.project(b, mask), w["mf"][0], origin, block)
+    t_as = time.perf_counter() - t0
+    vbox = np.prod([min(L, bl + 4) for L, bl in zip(w["dims"], block)])
+    t_a = t_as * np.prod(w["dims"]) / vbox
+    per_outer = t_a + k * nblocks * t_as
+    return {"value": float(outer_iters * per_outer), "t_sample": t_as,
+            "sample": (f"one FP64 oracle A_s apply on one 8^3x16 block box ({t_as:.1f} s), "
+                       f"scaled to {outer_iters} outer iterations x (A + {k} x {nblocks} A_s)")}
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [1])
+    except Exception:
+        return 1
+
+
+# ----------------------------------------------------------------------------
+# GB300 arm
+# ----------------------------------------------------------------------------
+def flush_l2(buf):
+    buf.add_(1)
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    w = syn.WORKLOADS[WORKLOAD]
+    dims, Ls, mf = w["dims"], w["Ls"], w["mf"][0]
+    Uc = syn.gauge_field(dims, w["eps"], 1000 + w["id"])
+    src = syn.half_field(dims, Ls, 2000 + w["id"] + rank)
+    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"], device=dev)
+    ctx.gauge_load(Uc)
+    stream = torch.cuda.current_stream()
+    V4 = int(np.prod(dims))
+    Vh = V4 // 2
+    l2_flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
+
+    # --- hop kernel bandwidth (FP32, the solver's outer launch shape) ---------
+    canon = torch.from_numpy(src[None].copy()).cuda()
+    fin = ctx.new_field("fp32")
+    fout = ctx.new_field("fp32")
+    ctx.field_import(fin, "fp32", canon)
+    alg_bytes = 2 * Vh * Ls * 24 * 4 + V4 * 4 * 18 * 4
+    for _ in range(5):
+        ctx.dslash_eo(fout, fin, 0, 0, "fp32", [mf])
+    times = []
+    for _ in range(30):
+        flush_l2(l2_flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.dslash_eo(fout, fin, 0, 0, "fp32", [mf])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    t_hop = statistics.median(times)
+    hop_gbs = alg_bytes / t_hop / 1e9
+
+    # --- solves -----------------------------------------------------------------
+    b = canon
+    x = torch.zeros_like(b)
+    p_ms = dwf.default_params(inner_iters=6, block=w["block"], inner="fp16", outer="fp32",
+                              tol=1e-10)
+    p_plain = dwf.default_params(inner_iters=0, outer="fp32", tol=1e-10)
+
+    def timed_solves(prm, n, collect):
+        out = []
+        for _ in range(n):
+            flush_l2(l2_flush)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = ctx.solve(x, b, [mf], prm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            if collect:
+                out.append((e0.elapsed_time(e1) * 1e-3, st, info[0]))
+        return out
+
+    timed_solves(p_plain, max(1, args.warmup // 2), False)
+    plain = timed_solves(p_plain, max(1, args.steps // 2 + 1), True)
+    timed_solves(p_ms, args.warmup, False)
+    with ClockSampler(dev) as clk:
+        ms = timed_solves(p_ms, args.steps, True)
+    # e2e: host buffers, copies inside the timed region
+    bh = torch.from_numpy(src[None].copy()).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    p_e2e = dwf.default_params(inner_iters=6, block=w["block"], inner="fp16", outer="fp32",
+                               tol=1e-10, io_on_host=1)
+    ctx.solve(xh, bh, [mf], p_e2e)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush_l2(l2_flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = ctx.solve(xh, bh, [mf], p_e2e)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+
+    t_ms = statistics.mean(t for t, _, _ in ms)
+    t_plain = statistics.mean(t for t, _, _ in plain)
+    t_e2e = statistics.mean(e2e_t)
+    if dist:
+        import torch.distributed as td
+        v = torch.tensor([t_ms, t_plain, t_e2e], dtype=torch.float64, device="cuda")
+        td.all_reduce(v, op=td.ReduceOp.MAX)
+        t_ms, t_plain, t_e2e = v.tolist()
+    info_ms, info_plain = ms[-1][2], plain[-1][2]
+    ok = all(st == 0 and i["converged"] for _, st, i in ms + plain)
+    k = 6
+    nblocks = int(np.prod([d // bl for d, bl in zip(dims, w["block"])]))
+    launches_ms = (1 + 1 + (6 * k + 1) + 2 + info_ms["outer_iters"] * (6 + 6 * k + 1)
+                   + info_ms["reliable_updates"] * (6 + 6 * k + 2) + 1)
+    peak, kind = peaks()
+    res = {
+        "metric": METRIC,
+        "value": round(t_ms, 6),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_ms * 1e3, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "16^3x32", "Ls": Ls, "b": w["b"], "c": w["c"],
+                   "M5": w["M5"], "mf": mf, "gauge_eps": w["eps"], "block": "8^3x16",
+                   "nblocks": nblocks, "inner_iters": k, "inner": "fp16+scale", "outer": "fp32",
+                   "reductions": "fp64", "tol": 1e-10, "parallelism": f"replicas{world}",
+                   "l2": "solve working set > L2 (about 1.3 GB); 256 MB L2 flush between steps"},
+        "mspcg": {"seconds": round(t_ms, 6), "outer_iters": info_ms["outer_iters"],
+                  "inner_iters_total": info_ms["inner_iters_total"],
+                  "reliable_updates": info_ms["reliable_updates"],
+                  "true_resid": info_ms["true_resid"]},
+        "plain_cg": {"seconds": round(t_plain, 6), "outer_iters": info_plain["outer_iters"],
+                     "reliable_updates": info_plain["reliable_updates"],
+                     "true_resid": info_plain["true_resid"]},
+        "mspcg_speedup_vs_plain": round(t_plain / t_ms, 4),
+        "all_converged": ok,
+        "dslash": {"kernel": "hop_kernel<F32,DAG=0,PRE=1> (M^4 = -1/2 Dhop M_phi)",
+                   "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
+                   "gbs": round(hop_gbs, 1), "frac_of_8tbs_nominal": round(hop_gbs / 8000, 4)},
+        "roofline": {"bound": "hbm", "achieved": round(hop_gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(hop_gbs / peak, 4), "traffic": None,
+                     "kernel": "hop_kernel<F32,0,1>", "peak_kind": kind},
+        "e2e": {"value": round(t_e2e, 6), "unit": "s",
+                "h2d_bytes_per_step": int(bh.numel() * 16), "d2h_bytes_per_step": int(xh.numel() * 16)},
+        "gpu_launches": int(launches_ms),
+        "clocks": clk.summary(),
+    }
+    return res, info_ms, nblocks
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_1811_08488_gb300 import synthetic as syn
+        w = syn.WORKLOADS[WORKLOAD]
+        # iteration count of the GB300 MSPCG solve of this workload (measured),
+        # used to scale the per-iteration sample
+        outer = int(os.environ.get("MSPCG_OUTER_ITERS", "300"))
+        nblocks = 16
+        vals = []
+        for i in range(args.warmup + args.steps):
+            s = cpu_sample(outer, 6, nblocks)
+            if i >= args.warmup:
+                vals.append(s["value"])
+        v = statistics.mean(vals)
+        cores = cpu_threads()
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": False, "data": "synthetic", "dtype": "f64",
+                          "config": {"workload": WORKLOAD},
+                          "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": cores,
+                                           "kind": "oracle", "sample": s["sample"]},
+                          "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+        dist = td
+    res, info_ms, nblocks = run_gpu(args, rank, world, dist)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            s = cpu_sample(info_ms["outer_iters"], 6, nblocks)
+            res["cpu_baseline"] = {"value": round(s["value"], 3), "unit": "s",
+                                   "cores": cpu_threads(), "kind": "oracle", "sample": s["sample"]}
+        print(json.dumps(res))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

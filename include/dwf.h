@@ -1,0 +1,227 @@
+/*
+ * dwf.h -- C ABI of the GB300 (sm_103a) multisplitting-preconditioned CG solver
+ * for the even-odd preconditioned Shamir/Moebius domain-wall-fermion system.
+ *
+ * Paper: J. Tu, "Solving DWF Dirac Equation Using Multisplitting Preconditioned
+ * Conjugate Gradient", LATTICE2018 (arXiv:1811.08488).
+ *
+ * Operator (paper Sec. 2.2, the even-odd block system and eq. (dirac_equation)):
+ *
+ *     [ M_5      M^4_eo ] [psi_e]   [phi_e]
+ *     [ M^4_oe   M_5    ] [psi_o] = [phi_o],    D_PC = M_5 - M^4_eo M_5^-1 M^4_oe,
+ *
+ * with M^4 = D^w M_phi (eq. for D^w). The paper defers the entries of M_5 and
+ * M_phi to Brower et al. (2014); this library uses the standard Moebius form
+ *
+ *     Dhop psi(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)
+ *     M^4         = -1/2 Dhop M_phi,      M_phi = b + c C,      M_5 = alpha + beta C,
+ *     alpha = b (4 - M5) + 1,   beta = c (4 - M5) - 1,
+ *     (C psi)_s   = P_- psi_{s+1} + P_+ psi_{s-1},  psi_{Ls} = -m_f psi_0, psi_{-1} = -m_f psi_{Ls-1},
+ *
+ * in the chiral gamma basis g_k = [[0,-i s_k],[i s_k,0]], g_4 = [[0,1],[1,0]],
+ * g_5 = diag(1,1,-1,-1), P_+- = (1 +- g_5)/2. Shamir is b = 1, c = 0.
+ * Boundary conditions: periodic in x, y, z; antiperiodic in t unless disabled.
+ * The solve is the normal equation D_PC^+ D_PC psi_e = b (eq. (normal_equation)).
+ *
+ * ---------------------------------------------------------------------------
+ * Layouts
+ * ---------------------------------------------------------------------------
+ * Sites: lexicographic index idx = ((t*Lz + z)*Ly + y)*Lx + x; parity
+ * (x+y+z+t) mod 2 (paper eq. parity); the half index of a site is idx/2, so the
+ * sites of one parity are numbered 0 .. V/2-1.
+ *
+ * Gauge field (input to dwf_gauge_load): complex128 U[t][z][y][x][mu][a][b],
+ * mu = 0..3 for x, y, z, t, U_mu(x) the SU(3) matrix on the link x -> x+mu.
+ *
+ * Canonical half field (import/export and mspcg_solve): complex numbers
+ * psi[rhs][s][t][z][y][xh][spin 4][colour 3], with x = 2*xh + ((parity+y+z+t)%2);
+ * complex128 (canon_is_fp32 = 0) or complex64 (canon_is_fp32 = 1).
+ *
+ * Native half field (all operator entry points): one right-hand side after
+ * another, each dwf_field_bytes(ctx, prec, 1) bytes (a multiple of 256).
+ * Inside one right-hand side, the 24 reals of (site h, s) -- ordered
+ * [spin][colour][re,im] -- are cut into 16-byte chunks, and chunk k of all Ls
+ * slices of a site is contiguous:
+ *     DWF_FP64: 12 chunks of 2 doubles,  byte offset ((h*12 + k)*Ls + s)*16
+ *     DWF_FP32:  6 chunks of 4 floats,   byte offset ((h*6  + k)*Ls + s)*16
+ *     DWF_FP16/BF16: 3 chunks of 8 halves, byte offset ((h*3 + k)*Ls + s)*16,
+ *         followed (at the next 256-byte boundary) by one float scale per
+ *         (h, s) at [h*Ls + s]; the stored value times the scale is the field.
+ * Convert with dwf_field_import / dwf_field_export.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions for every entry point
+ * ---------------------------------------------------------------------------
+ * - Field pointers are device pointers on the context's device unless stated.
+ * - The caller owns every field buffer and the stream; `stream` is a
+ *   cudaStream_t (NULL: the legacy default stream). Work is enqueued on it; the
+ *   call returns without synchronising unless stated.
+ * - `mf` is a HOST array of nrhs quark masses m_f (one per right-hand side).
+ * - `nrhs` is 1 .. DWF_MAX_RHS.
+ * - The context owns packed links, geometry tables, work buffers and plans; it
+ *   allocates them on first need and frees them in dwf_destroy.
+ * - A context must not be used from two host threads at once; work on two
+ *   streams of one context that shares the context's work buffers races.
+ * - The return code is the contract. On an error nothing is written to output
+ *   buffers unless stated, and dwf_last_error() describes the failure. Nothing
+ *   aborts the process.
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DWF_MAX_RHS 16
+#define DWF_MAX_LS 32
+
+typedef enum {
+  DWF_OK = 0,
+  DWF_ERR_INVALID_ARG = 1,   /* bad pointer, size, shape or parameter        */
+  DWF_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement  */
+  DWF_ERR_CUDA = 3,          /* a CUDA call failed; see dwf_last_error        */
+  DWF_ERR_NOT_CONVERGED = 4, /* maxiter reached; x and info are still filled  */
+  DWF_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired            */
+  DWF_ERR_NAN = 6,           /* a NaN/Inf appeared in a solver scalar         */
+  DWF_ERR_NO_GAUGE = 7       /* operator called before dwf_gauge_load         */
+} dwf_status;
+
+typedef enum { DWF_FP64 = 0, DWF_FP32 = 1, DWF_FP16 = 2, DWF_BF16 = 3 } dwf_prec;
+
+/* The action: lattice and DWF parameters (paper Sec. 2.2). */
+typedef struct {
+  int dims[4];        /* Lx, Ly, Lz, Lt; all even                            */
+  int Ls;             /* fifth-dimension extent, 2 .. DWF_MAX_LS              */
+  double b, c;        /* Moebius coefficients (Shamir: b = 1, c = 0)         */
+  double M5;          /* domain-wall height                                  */
+  int t_antiperiodic; /* 1: antiperiodic in t (default), 0: periodic          */
+} dwf_action;
+
+/* Solver parameters. Start from dwf_solver_params_default(). */
+typedef struct {
+  double tol;         /* stop when |b - A x| / |b| <= tol (recomputed residual) */
+  int maxiter;        /* maximum outer iterations                               */
+  int inner_iters;    /* k fixed inner CG iterations per block; 0 = plain CG    */
+  int block[4];       /* sub-lattice extents (even, dividing dims)              */
+  dwf_prec outer;     /* DWF_FP64 or DWF_FP32 (FP32: FP64 reliable updates)     */
+  dwf_prec inner;     /* DWF_FP32, DWF_FP16 or DWF_BF16 block-solve storage     */
+  double delta;       /* reliable update when |r| < delta * max|r| since last   */
+  int snake;          /* 1: A_s = P_s A P_s (snake terms), 0: per-hop Dirichlet */
+  int use_graph;      /* 1: replay the iteration from a captured CUDA graph     */
+  int io_on_host;     /* mspcg_solve: 1 = x and b are host pointers             */
+  int check_every;    /* outer iterations between host convergence checks      */
+} dwf_solver_params;
+
+/* Per right-hand-side result of mspcg_solve. */
+typedef struct {
+  int outer_iters;       /* outer (Algorithm 1) iterations                   */
+  int inner_iters_total; /* outer_iters * k                                  */
+  int reliable_updates;  /* FP64 residual recomputations                     */
+  int converged;         /* 1 when true_resid <= tol                         */
+  double true_resid;     /* |b - A x| / |b| recomputed in FP64               */
+  double seconds;        /* wall time of the whole call (same for all rhs)   */
+} dwf_solve_info;
+
+typedef struct dwf_ctx dwf_ctx;
+
+/* Create a context on CUDA device `device` for action `a`.
+ * Errors: INVALID_ARG for odd or non-positive extents, Ls out of range;
+ * CUDA when the device cannot be used. On error *ctx is NULL. */
+dwf_status dwf_create(dwf_ctx **ctx, int device, const dwf_action *a);
+
+/* Free everything the context owns. NULL is accepted. The caller must make
+ * sure no work that uses the context is still running. */
+void dwf_destroy(dwf_ctx *ctx);
+
+/* Message of the last error on this context ("" if none). The string is owned
+ * by the context and valid until the next call on it. NULL ctx: last
+ * dwf_create failure. */
+const char *dwf_last_error(const dwf_ctx *ctx);
+
+/* Fill *p with the defaults: tol 1e-10, maxiter 100000, inner_iters 6,
+ * block = {0,0,0,0} (must be set for MSPCG), outer FP32, inner FP16,
+ * delta 0.1, snake 1, use_graph 1, io_on_host 0, check_every 10. */
+void dwf_solver_params_default(dwf_solver_params *p);
+
+/* Load the gauge field U (layout above; host pointer if on_device == 0).
+ * Packs FP64, FP32 and FP16 copies of the links with the antiperiodic time
+ * sign folded into the links that cross t = Lt-1 -> 0, and invalidates every
+ * cached block plan. Synchronous. Errors: INVALID_ARG (NULL U), CUDA. */
+dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device);
+
+/* Bytes of a native half field of precision `prec` with nrhs right-hand sides. */
+size_t dwf_field_bytes(const dwf_ctx *ctx, dwf_prec prec, int nrhs);
+
+/* Canonical -> native (import) and native -> canonical (export) conversion of
+ * parity half fields (layouts above). Conversion to FP16/BF16 computes the
+ * per-(site, s) scale. Errors: INVALID_ARG. */
+dwf_status dwf_field_import(dwf_ctx *ctx, void *native_out, dwf_prec prec,
+                            const void *canon_in, int canon_is_fp32, int nrhs,
+                            void *stream);
+dwf_status dwf_field_export(dwf_ctx *ctx, void *canon_out, int canon_is_fp32,
+                            const void *native_in, dwf_prec prec, int nrhs,
+                            void *stream);
+
+/* Hopping block M^4 (paper Sec. 2.2, M^4_{eo/oe} = D^w M_phi):
+ *   dagger = 0:  out = -1/2 Dhop (M_phi in)            (M^4_eo or M^4_oe)
+ *   dagger = 1:  out = -1/2 M_phi^+ Dhop^+ in          ((M^4)^+)
+ * `in` lives on parity 1 - out_parity, `out` on out_parity (0 even, 1 odd).
+ * prec: DWF_FP64 or DWF_FP32 (native fields). out must not alias in. */
+dwf_status dwf_dslash_eo(dwf_ctx *ctx, void *out, const void *in, int out_parity,
+                         int dagger, dwf_prec prec, int nrhs, const double *mf,
+                         void *stream);
+
+/* out = M_5 in, or M_5^+ in (dagger = 1): the 4D-diagonal block of the
+ * even-odd system (paper Sec. 2.2). FP64 or FP32 native fields. */
+dwf_status dwf_m5(dwf_ctx *ctx, void *out, const void *in, int dagger,
+                  dwf_prec prec, int nrhs, const double *mf, void *stream);
+
+/* out = M_5^-1 in, or M_5^-+ in, as used in D_PC and phi_hat (paper eq.
+ * (dirac_equation)); computed per chirality by the closed form
+ * [alpha (1 + m_f r^Ls)]^-1 sum_{k<Ls} r^k S^k, r = -beta/alpha. */
+dwf_status dwf_m5inv(dwf_ctx *ctx, void *out, const void *in, int dagger,
+                     dwf_prec prec, int nrhs, const double *mf, void *stream);
+
+/* out = D_PC in (dagger = 0) or D_PC^+ in (dagger = 1), even parity fields
+ * (paper eq. (dirac_equation)). */
+dwf_status dwf_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger,
+                   dwf_prec prec, int nrhs, const double *mf, void *stream);
+
+/* out = D_PC^+ D_PC in (paper eq. (normal_equation), eq. (DdagD)). */
+dwf_status dwf_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec,
+                     int nrhs, const double *mf, void *stream);
+
+/* Block operator of the multisplitting (paper Sec. 2.3): out = (+)_s A_s in,
+ * A_s = P_s D_PC^+ D_PC P_s (snake = 1) or the per-hop Dirichlet operator
+ * (snake = 0), on the blocks of params->block, computed in params->inner
+ * storage precision. in/out: FP32 native even fields. */
+dwf_status dwf_block_apply(dwf_ctx *ctx, void *out, const void *in,
+                           const dwf_solver_params *params, int nrhs,
+                           const double *mf, void *stream);
+
+/* The multisplitting preconditioner (paper Sec. 2.4): z = M^-1 r with
+ * M = (+)_s A_s, each A_s z_s = r_s solved by params->inner_iters CG iterations
+ * from a zero guess with block-local scalars. in/out: FP32 native even fields. */
+dwf_status dwf_block_precond(dwf_ctx *ctx, void *z, const void *r,
+                             const dwf_solver_params *params, int nrhs,
+                             const double *mf, void *stream);
+
+/* Solve D_PC^+ D_PC x = b for nrhs right-hand sides with Algorithm 1 (MSPCG;
+ * plain CG when params->inner_iters == 0). x and b are canonical complex128
+ * even half fields (device pointers, or host pointers when params->io_on_host).
+ * Outer iterations run in params->outer precision with FP64 reductions; with
+ * FP32 outer precision the residual is recomputed in FP64 (reliable update)
+ * whenever |r| fell by params->delta, and at convergence. `info` (host array
+ * of nrhs) is filled on success and on NOT_CONVERGED. Synchronous: returns
+ * when x is written. Errors: INVALID_ARG, NO_GAUGE, NOT_CONVERGED, NAN, CUDA. */
+dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs,
+                       const double *mf, const dwf_solver_params *params,
+                       dwf_solve_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWF_H */

@@ -1,0 +1,291 @@
+// The C ABI (include/dwf.h): argument checks, context management, dispatch.
+#include <cstring>
+#include <exception>
+
+#include "solver.cuh"
+
+using dwf::DevBuf;
+using dwf::Error;
+
+static thread_local std::string g_create_error;
+
+dwf_ctx::~dwf_ctx() {
+  solver_plans.clear();
+  block_plans.clear();
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+#define API_TRY(ctx) try {
+#define API_CATCH(ctx)                                                   \
+  }                                                                      \
+  catch (const Error &e) {                                               \
+    if (ctx) (ctx)->last_error = e.msg;                                  \
+    return e.code;                                                       \
+  }                                                                      \
+  catch (const std::exception &e) {                                      \
+    if (ctx) (ctx)->last_error = e.what();                               \
+    return DWF_ERR_CUDA;                                                 \
+  }                                                                      \
+  if (ctx) (ctx)->last_error.clear();                                    \
+  return DWF_OK;
+
+static void check_common(dwf_ctx *ctx, int nrhs, const double *mf) {
+  DWF_REQUIRE(ctx, DWF_ERR_INVALID_ARG, "null context");
+  DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_RHS, DWF_ERR_INVALID_ARG, "nrhs out of range");
+  DWF_REQUIRE(mf != nullptr, DWF_ERR_INVALID_ARG, "null mass array");
+  for (int r = 0; r < nrhs; ++r)
+    DWF_REQUIRE(mf[r] == mf[r], DWF_ERR_INVALID_ARG, "NaN quark mass");
+  DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+}
+
+static void check_prec_op(dwf_prec p) {
+  DWF_REQUIRE(p == DWF_FP64 || p == DWF_FP32, DWF_ERR_INVALID_ARG,
+              "operator entry points take DWF_FP64 or DWF_FP32 fields");
+}
+
+extern "C" {
+
+dwf_status dwf_create(dwf_ctx **out, int device, const dwf_action *a) {
+  if (!out) return DWF_ERR_INVALID_ARG;
+  *out = nullptr;
+  dwf_ctx *ctx = nullptr;
+  try {
+    DWF_REQUIRE(a != nullptr, DWF_ERR_INVALID_ARG, "null action");
+    for (int m = 0; m < 4; ++m)
+      DWF_REQUIRE(a->dims[m] >= 2 && a->dims[m] % 2 == 0, DWF_ERR_INVALID_ARG,
+                  "lattice extents must be even and >= 2");
+    DWF_REQUIRE(a->Ls >= 2 && a->Ls <= DWF_MAX_LS, DWF_ERR_INVALID_ARG, "Ls out of range");
+    const double alpha = a->b * (4.0 - a->M5) + 1.0;
+    DWF_REQUIRE(alpha != 0.0 && a->b == a->b && a->c == a->c, DWF_ERR_INVALID_ARG,
+                "M_5 is singular for these b, M5");
+    const long long v4 = (long long)a->dims[0] * a->dims[1] * a->dims[2] * a->dims[3];
+    DWF_REQUIRE(v4 * a->Ls < (1LL << 31) / 8, DWF_ERR_INVALID_ARG, "lattice too large");
+    int ndev = 0;
+    DWF_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    DWF_REQUIRE(device >= 0 && device < ndev, DWF_ERR_INVALID_ARG, "no such device");
+    DWF_CUDA_TRY(cudaSetDevice(device));
+    ctx = new dwf_ctx();
+    ctx->device = device;
+    ctx->act = *a;
+    dwf::build_geometry(ctx->geo, a->dims);
+    for (int p = 0; p < 2; ++p) {
+      ctx->nbr_dev[p].ensure(ctx->geo.nbr[p].size() * sizeof(int));
+      DWF_CUDA_TRY(cudaMemcpy(ctx->nbr_dev[p].p, ctx->geo.nbr[p].data(),
+                              ctx->geo.nbr[p].size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    DWF_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+    dwf::prepare_kernels();
+    *out = ctx;
+    return DWF_OK;
+  } catch (const Error &e) {
+    g_create_error = e.msg;
+    delete ctx;
+    return e.code;
+  } catch (const std::exception &e) {
+    g_create_error = e.what();
+    delete ctx;
+    return DWF_ERR_CUDA;
+  }
+}
+
+void dwf_destroy(dwf_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  delete ctx;
+}
+
+const char *dwf_last_error(const dwf_ctx *ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+void dwf_solver_params_default(dwf_solver_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tol = 1e-10;
+  p->maxiter = 100000;
+  p->inner_iters = 6;
+  p->outer = DWF_FP32;
+  p->inner = DWF_FP16;
+  p->delta = 0.1;
+  p->snake = 1;
+  p->use_graph = 1;
+  p->io_on_host = 0;
+  p->check_every = 10;
+}
+
+dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && U, DWF_ERR_INVALID_ARG, "null context or gauge field");
+  DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+  const size_t n = (size_t)ctx->geo.V4 * 4 * 18;
+  DevBuf tmp;
+  const double *src = U;
+  if (!on_device) {
+    tmp.ensure(n * sizeof(double));
+    DWF_CUDA_TRY(cudaMemcpy(tmp.p, U, n * sizeof(double), cudaMemcpyHostToDevice));
+    src = tmp.as<double>();
+  }
+  const size_t nrec = (size_t)ctx->geo.V4 * 4;
+  ctx->links[0].ensure(nrec * 144);
+  ctx->links[1].ensure(nrec * 80);
+  ctx->links[2].ensure(nrec * 48);
+  dwf::launch_pack_links(src, ctx->links[0].c(), ctx->links[1].c(), ctx->links[2].c(),
+                         ctx->act.dims, ctx->act.t_antiperiodic, nullptr);
+  DWF_CUDA_TRY(cudaDeviceSynchronize());
+  for (auto &kv : ctx->block_plans) kv.second->links_valid = false;
+  ctx->have_gauge = true;
+  API_CATCH(ctx)
+}
+
+size_t dwf_field_bytes(const dwf_ctx *ctx, dwf_prec prec, int nrhs) {
+  if (!ctx || nrhs < 0) return 0;
+  return dwf::field_rhs_bytes(prec, ctx->geo.Vh, ctx->act.Ls) * (size_t)nrhs;
+}
+
+dwf_status dwf_field_import(dwf_ctx *ctx, void *native_out, dwf_prec prec, const void *canon_in,
+                            int canon_is_fp32, int nrhs, void *stream) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && native_out && canon_in, DWF_ERR_INVALID_ARG, "null argument");
+  DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_RHS, DWF_ERR_INVALID_ARG, "nrhs out of range");
+  DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+  dwf::launch_import(prec, (char *)native_out,
+                     (long long)dwf::field_rhs_bytes(prec, ctx->geo.Vh, ctx->act.Ls), canon_in,
+                     canon_is_fp32, ctx->geo.Vh, ctx->act.Ls, ctx->act.dims, nrhs,
+                     (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_field_export(dwf_ctx *ctx, void *canon_out, int canon_is_fp32,
+                            const void *native_in, dwf_prec prec, int nrhs, void *stream) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && native_in && canon_out, DWF_ERR_INVALID_ARG, "null argument");
+  DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_RHS, DWF_ERR_INVALID_ARG, "nrhs out of range");
+  DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+  dwf::launch_export(prec, canon_out, canon_is_fp32, (const char *)native_in,
+                     (long long)dwf::field_rhs_bytes(prec, ctx->geo.Vh, ctx->act.Ls),
+                     ctx->geo.Vh, ctx->act.Ls, ctx->act.dims, nrhs, (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_dslash_eo(dwf_ctx *ctx, void *out, const void *in, int out_parity, int dagger,
+                         dwf_prec prec, int nrhs, const double *mf, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(out_parity == 0 || out_parity == 1, DWF_ERR_INVALID_ARG, "parity must be 0 or 1");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::apply_dslash(ctx, out, in, out_parity, dagger ? 1 : 0, prec, nrhs, mf,
+                    (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+static dwf_status ls_entry(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec,
+                           int nrhs, const double *mf, void *stream, bool inverse) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(out && in, DWF_ERR_INVALID_ARG, "null fields");
+  dwf::LsCoef c[DWF_MAX_RHS];
+  for (int r = 0; r < nrhs; ++r)
+    c[r] = inverse ? dwf::coef_m5inv(ctx->act, mf[r], 1.0) : dwf::coef_m5(ctx->act, mf[r], 1.0);
+  dwf::launch_ls_op(prec, (char *)out, (const char *)in,
+                    (long long)dwf::field_rhs_bytes(prec, ctx->geo.Vh, ctx->act.Ls), ctx->geo.Vh,
+                    ctx->act.Ls, dagger ? 1 : 0, inverse ? 1 : 0, nrhs, c, (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_m5(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec, int nrhs,
+                  const double *mf, void *stream) {
+  return ls_entry(ctx, out, in, dagger, prec, nrhs, mf, stream, false);
+}
+
+dwf_status dwf_m5inv(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec,
+                     int nrhs, const double *mf, void *stream) {
+  return ls_entry(ctx, out, in, dagger, prec, nrhs, mf, stream, true);
+}
+
+dwf_status dwf_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec, int nrhs,
+                   const double *mf, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_mpc(ctx, out, in, dagger ? 1 : 0, prec, nrhs, mf, w, (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec, int nrhs,
+                     const double *mf, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_mdagm(ctx, out, in, prec, nrhs, mf, w, nullptr, nullptr, (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+static void check_params(const dwf_solver_params *p) {
+  DWF_REQUIRE(p != nullptr, DWF_ERR_INVALID_ARG, "null solver parameters");
+}
+
+dwf_status dwf_block_apply(dwf_ctx *ctx, void *out, const void *in,
+                           const dwf_solver_params *params, int nrhs, const double *mf,
+                           void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_params(params);
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  cudaStream_t st = (cudaStream_t)stream;
+  dwf::BlockPlan *bp = dwf::get_block_plan(ctx, params->block, params->inner, nrhs, st);
+  dwf::BlockArgs B = dwf::block_args(ctx, bp, (char *)out, (const char *)in, nullptr, 0, nullptr);
+  dwf::block_gather(bp->inner, B, nrhs, st);
+  dwf::block_apply_A(ctx, bp, params->snake, nrhs, mf, false, nullptr, st);
+  dwf::block_export(bp->inner, B, bp->fAp, nrhs, st);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_block_precond(dwf_ctx *ctx, void *z, const void *r,
+                             const dwf_solver_params *params, int nrhs, const double *mf,
+                             void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_params(params);
+  DWF_REQUIRE(z && r && z != r, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(params->inner_iters >= 1, DWF_ERR_INVALID_ARG, "inner_iters must be >= 1");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  cudaStream_t st = (cudaStream_t)stream;
+  dwf::BlockPlan *bp = dwf::get_block_plan(ctx, params->block, params->inner, nrhs, st);
+  dwf::block_precondition(ctx, bp, (char *)z, (const char *)r, params->inner_iters,
+                          params->snake, nrhs, mf, nullptr, 0, nullptr, st);
+  API_CATCH(ctx)
+}
+
+dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
+                       const dwf_solver_params *params, dwf_solve_info *info, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_params(params);
+  DWF_REQUIRE(x && b, DWF_ERR_INVALID_ARG, "null x or b");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  DWF_REQUIRE(params->check_every >= 1, DWF_ERR_INVALID_ARG, "check_every must be >= 1");
+  DWF_REQUIRE(params->delta > 0 && params->delta < 1, DWF_ERR_INVALID_ARG,
+              "delta must be in (0, 1)");
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->own_stream;
+  if (!stream) DWF_CUDA_TRY(cudaDeviceSynchronize());
+  dwf_status s = dwf::solve(ctx, x, b, nrhs, mf, params, info, st);
+  if (s != DWF_OK) {
+    ctx->last_error = s == DWF_ERR_NOT_CONVERGED ? "not converged within maxiter"
+                      : s == DWF_ERR_NAN         ? "NaN or Inf in a solver scalar"
+                                                 : "solver error";
+    return s;
+  }
+  API_CATCH(ctx)
+}
+
+}  // extern "C"

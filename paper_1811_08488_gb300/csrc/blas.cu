@@ -1,0 +1,447 @@
+// Vector updates and reductions of the outer preconditioned CG (Algorithm 1)
+// and of the block-local inner CG (Sec. 2.4: k fixed CG iterations per block,
+// block-local scalars, zero initial guess).
+//
+// Reductions accumulate in FP64, one partial per CTA; the last CTA of a group
+// sums the partials in a fixed order, so results are bitwise reproducible. The
+// scalars alpha and beta are formed on the device from those sums.
+#include <type_traits>
+
+#include "blas.cuh"
+#include "device_common.cuh"
+
+namespace dwf {
+
+constexpr int kOuterCtas = 152 * 4;
+constexpr int kBlasThreads = 256;
+int outer_ctas() { return kOuterCtas; }
+
+// Group i of a native field: the 4 reals [4c, 4c+4) of (site, s), numbered in
+// FP32 chunk order, i = (site * 6 + c) * Ls + s. In an FP32 field this is the
+// float4 at index i; in an FP64 field it is the two double2 chunks 2c and
+// 2c+1 of (site, s). Kernels that mix precisions therefore meet the same
+// (site, s, component) on both sides.
+template <class S>
+__device__ __forceinline__ void ld4(const char *p, long long i, int Ls, double v[4]) {
+  if constexpr (std::is_same<S, F32>::value) {
+    float4 q = reinterpret_cast<const float4 *>(p)[i];
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const long long site = i / (6 * Ls);
+    const int rem = (int)(i - site * 6 * Ls), c = rem / Ls, s = rem - c * Ls;
+    const long long j = (site * 12 + 2 * c) * Ls + s;
+    double2 a = reinterpret_cast<const double2 *>(p)[j];
+    double2 b = reinterpret_cast<const double2 *>(p)[j + Ls];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+template <class S>
+__device__ __forceinline__ void st4(char *p, long long i, int Ls, const double v[4]) {
+  if constexpr (std::is_same<S, F32>::value) {
+    reinterpret_cast<float4 *>(p)[i] =
+        make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  } else {
+    const long long site = i / (6 * Ls);
+    const int rem = (int)(i - site * 6 * Ls), c = rem / Ls, s = rem - c * Ls;
+    const long long j = (site * 12 + 2 * c) * Ls + s;
+    reinterpret_cast<double2 *>(p)[j] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[j + Ls] = make_double2(v[2], v[3]);
+  }
+}
+template <class S>
+__device__ __forceinline__ void round4(double v[4]) {
+  if constexpr (std::is_same<S, F32>::value) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (double)(float)v[k];
+  }
+}
+
+#define FLAT_LOOP(n4)                                                              \
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n4); \
+       i += (long long)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------
+// Outer solve
+// ---------------------------------------------------------------------------
+// r64 = b; rlo = b; |b|^2 -> bb and rr (and rz for plain CG); iter = 0.
+template <class SL>
+__global__ void __launch_bounds__(kBlasThreads) init_kernel(const OuterArgs A) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  if (A.skip && A.skip[rhs]) return;
+  const long long o64 = rhs * A.rs64, olo = rhs * A.rslo;
+  double acc = 0.0;
+  FLAT_LOOP(A.n4) {
+    double v[4];
+    ld4<F64>(A.b64 + o64, i, A.Ls, v);
+    st4<F64>(A.r64 + o64, i, A.Ls, v);
+    st4<SL>(A.rlo + olo, i, A.Ls, v);
+    acc += v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  }
+  acc = cta_sum(acc, red);
+  double tot;
+  if (group_reduce(acc, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
+                   A.counters + rhs, tot)) {
+    OuterScalars *sc = A.scal + rhs;
+    sc->bb = tot;
+    sc->rr = tot;
+    if (A.plain) sc->rz = tot;
+    sc->iter = 0;
+  }
+}
+
+// x += alpha p; r -= alpha Ap; |r|^2 with alpha = <r,z> / <p,Ap> (Algorithm 1).
+template <class SL>
+__global__ void __launch_bounds__(kBlasThreads) axpy_xr_kernel(const OuterArgs A) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  if (A.skip && A.skip[rhs]) return;
+  OuterScalars *sc = A.scal + rhs;
+  const double pAp = sc->pAp;
+  const double alpha = pAp != 0.0 ? sc->rz / pAp : 0.0;
+  const long long o = rhs * A.rslo;
+  double acc = 0.0;
+  FLAT_LOOP(A.n4) {
+    double x[4], r[4], p[4], q[4];
+    ld4<SL>(A.xlo + o, i, A.Ls, x);
+    ld4<SL>(A.rlo + o, i, A.Ls, r);
+    ld4<SL>(A.p + o, i, A.Ls, p);
+    ld4<SL>(A.Ap + o, i, A.Ls, q);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      x[k] += alpha * p[k];
+      r[k] -= alpha * q[k];
+    }
+    st4<SL>(A.xlo + o, i, A.Ls, x);
+    st4<SL>(A.rlo + o, i, A.Ls, r);
+    round4<SL>(r);
+    acc += r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+  }
+  acc = cta_sum(acc, red);
+  double tot;
+  if (group_reduce(acc, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
+                   A.counters + rhs, tot)) {
+    sc->rr = tot;
+    sc->alpha = alpha;
+    sc->hist_rr[sc->iter % kHistory] = tot;
+    if (A.plain) sc->rz_new = tot;
+  }
+}
+
+// beta = <r',z'> / <r,z>; p = z + beta p (z = r for plain CG); iter++.
+template <class SL>
+__global__ void __launch_bounds__(kBlasThreads) xpay_p_kernel(const OuterArgs A) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  if (A.skip && A.skip[rhs]) return;
+  OuterScalars *sc = A.scal + rhs;
+  const double rz = sc->rz, rzn = sc->rz_new;
+  const double beta = rz != 0.0 ? rzn / rz : 0.0;
+  const long long o = rhs * A.rslo;
+  const char *z = A.plain ? A.rlo : A.z;
+  FLAT_LOOP(A.n4) {
+    double p[4], zz[4];
+    ld4<SL>(A.p + o, i, A.Ls, p);
+    ld4<SL>(z + o, i, A.Ls, zz);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = zz[k] + beta * p[k];
+    st4<SL>(A.p + o, i, A.Ls, p);
+  }
+  double tot;
+  if (group_reduce(0.0, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
+                   A.counters + rhs, tot)) {
+    sc->rz = rzn;
+    sc->beta = beta;
+    sc->iter += 1;
+  }
+  (void)red;
+}
+
+// p = z (or r for plain CG).
+template <class SL>
+__global__ void __launch_bounds__(kBlasThreads) copy_p_kernel(const OuterArgs A) {
+  const int rhs = blockIdx.y;
+  if (A.skip && A.skip[rhs]) return;
+  const long long o = rhs * A.rslo;
+  const char *z = A.plain ? A.rlo : A.z;
+  FLAT_LOOP(A.n4) {
+    double v[4];
+    ld4<SL>(z + o, i, A.Ls, v);
+    st4<SL>(A.p + o, i, A.Ls, v);
+  }
+}
+
+// x64 += xlo; xlo = 0 (the FP64 accumulation of a reliable update).
+template <class SL>
+__global__ void __launch_bounds__(kBlasThreads) promote_kernel(const OuterArgs A) {
+  const int rhs = blockIdx.y;
+  if (A.skip && A.skip[rhs]) return;
+  const long long o64 = rhs * A.rs64, olo = rhs * A.rslo;
+  FLAT_LOOP(A.n4) {
+    double x[4], d[4];
+    ld4<F64>(A.x64 + o64, i, A.Ls, x);
+    ld4<SL>(A.xlo + olo, i, A.Ls, d);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] += d[k];
+    st4<F64>(A.x64 + o64, i, A.Ls, x);
+    const double z[4] = {0, 0, 0, 0};
+    st4<SL>(A.xlo + olo, i, A.Ls, z);
+  }
+}
+
+// r64 = b - A x64 (FP64); rlo = r64; |r64|^2 -> rr (and rz for plain CG).
+template <class SL>
+__global__ void __launch_bounds__(kBlasThreads) ru_residual_kernel(const OuterArgs A) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  if (A.skip && A.skip[rhs]) return;
+  const long long o64 = rhs * A.rs64, olo = rhs * A.rslo;
+  double acc = 0.0;
+  FLAT_LOOP(A.n4) {
+    double b[4], ax[4];
+    ld4<F64>(A.b64 + o64, i, A.Ls, b);
+    ld4<F64>(A.Ax64 + o64, i, A.Ls, ax);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] -= ax[k];
+    st4<F64>(A.r64 + o64, i, A.Ls, b);
+    st4<SL>(A.rlo + olo, i, A.Ls, b);
+    acc += b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+  }
+  acc = cta_sum(acc, red);
+  double tot;
+  if (group_reduce(acc, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
+                   A.counters + rhs, tot)) {
+    OuterScalars *sc = A.scal + rhs;
+    sc->rr = tot;
+    if (A.plain) sc->rz = tot;
+  }
+}
+
+__global__ void set_rz_kernel(OuterScalars *scal, const int *skip, int nrhs) {
+  const int r = threadIdx.x;
+  if (r < nrhs && !(skip && skip[r])) scal[r].rz = scal[r].rz_new;
+}
+
+#define DISPATCH_LO(lo, KERNEL, ...)                                        \
+  do {                                                                      \
+    dim3 g(kOuterCtas, nrhs);                                               \
+    if ((lo) == DWF_FP64)                                                   \
+      KERNEL<F64><<<g, kBlasThreads, 0, st>>>(__VA_ARGS__);                 \
+    else                                                                    \
+      KERNEL<F32><<<g, kBlasThreads, 0, st>>>(__VA_ARGS__);                 \
+    DWF_CUDA_TRY(cudaGetLastError());                                       \
+  } while (0)
+
+void outer_init(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st) {
+  DISPATCH_LO(lo, init_kernel, A);
+}
+void outer_axpy_xr(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st) {
+  DISPATCH_LO(lo, axpy_xr_kernel, A);
+}
+void outer_xpay_p(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st) {
+  DISPATCH_LO(lo, xpay_p_kernel, A);
+}
+void outer_copy_p(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st) {
+  DISPATCH_LO(lo, copy_p_kernel, A);
+}
+void outer_promote(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st) {
+  DISPATCH_LO(lo, promote_kernel, A);
+}
+void outer_ru_residual(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st) {
+  DISPATCH_LO(lo, ru_residual_kernel, A);
+}
+void outer_set_rz(const OuterArgs &A, int nrhs, cudaStream_t st) {
+  set_rz_kernel<<<1, 32, 0, st>>>(A.scal, A.skip, nrhs);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Inner block CG. Thread (i, s) of block b; grid (tiles, nblocks, nrhs).
+// ---------------------------------------------------------------------------
+int block_tiles(int n_b, int Ls) {
+  return (int)(((long long)n_b * Ls + kBlasThreads - 1) / kBlasThreads);
+}
+
+template <class SI>
+__global__ void __launch_bounds__(kBlasThreads) blk_gather_kernel(const BlockArgs B) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.z, b = blockIdx.y;
+  if (B.skip && B.skip[rhs]) return;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
+  double acc = 0.0;
+  if (i < B.n_b) {
+    const int h = B.gmap[(size_t)b * B.n_b + i];
+    float v[24];
+    load24<F32>(B.rglob + rhs * B.grs, 0, h, s, B.Ls, v);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc += (double)v[k] * v[k];
+    const long long off = rhs * B.r.rstride + b * B.r.bstride;
+    store24<SI>(B.r.data + off, B.r.scale_off, i, s, B.Ls, v);
+    store24<SI>(B.p.data + rhs * B.p.rstride + b * B.p.bstride, B.p.scale_off, i, s, B.Ls, v);
+    float zero[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) zero[k] = 0.f;
+    store24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, i, s, B.Ls, zero);
+  }
+  acc = cta_sum(acc, red);
+  const int grp = rhs * B.nblocks + b;
+  double tot;
+  if (group_reduce(acc, B.partials + (size_t)grp * gridDim.x, gridDim.x, blockIdx.x,
+                   B.counters + grp, tot))
+    B.rr[grp] = tot;
+}
+
+// alpha_b = rr_b / pAp_b; x += alpha p; unless LAST: r -= alpha Ap, |r|^2 -> rr_new.
+template <class SI, bool LAST>
+__global__ void __launch_bounds__(kBlasThreads) blk_xr_kernel(const BlockArgs B) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.z, b = blockIdx.y;
+  if (B.skip && B.skip[rhs]) return;
+  const int grp = rhs * B.nblocks + b;
+  const double pAp = B.pAp[grp];
+  const float alpha = (float)(pAp != 0.0 ? B.rr[grp] / pAp : 0.0);
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
+  double acc = 0.0;
+  if (i < B.n_b) {
+    float x[24], p[24];
+    char *xb = B.x.data + rhs * B.x.rstride + b * B.x.bstride;
+    load24<F32>(xb, 0, i, s, B.Ls, x);
+    load24<SI>(B.p.data + rhs * B.p.rstride + b * B.p.bstride, B.p.scale_off, i, s, B.Ls, p);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) x[k] += alpha * p[k];
+    store24<F32>(xb, 0, i, s, B.Ls, x);
+    if (!LAST) {
+      float r[24], q[24];
+      char *rb = B.r.data + rhs * B.r.rstride + b * B.r.bstride;
+      load24<SI>(rb, B.r.scale_off, i, s, B.Ls, r);
+      load24<SI>(B.Ap.data + rhs * B.Ap.rstride + b * B.Ap.bstride, B.Ap.scale_off, i, s, B.Ls,
+                 q);
+#pragma unroll
+      for (int k = 0; k < 24; ++k) {
+        r[k] -= alpha * q[k];
+        acc += (double)r[k] * r[k];
+      }
+      store24<SI>(rb, B.r.scale_off, i, s, B.Ls, r);
+    }
+  }
+  if (!LAST) {
+    acc = cta_sum(acc, red);
+    double tot;
+    if (group_reduce(acc, B.partials + (size_t)grp * gridDim.x, gridDim.x, blockIdx.x,
+                     B.counters + grp, tot))
+      B.rr_new[grp] = tot;
+  }
+}
+
+// beta_b = rr_new_b / rr_b; p = r + beta p; then rr_b = rr_new_b.
+template <class SI>
+__global__ void __launch_bounds__(kBlasThreads) blk_p_kernel(const BlockArgs B) {
+  const int rhs = blockIdx.z, b = blockIdx.y;
+  if (B.skip && B.skip[rhs]) return;
+  const int grp = rhs * B.nblocks + b;
+  const double rr = B.rr[grp];
+  const float beta = (float)(rr != 0.0 ? B.rr_new[grp] / rr : 0.0);
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
+  if (i < B.n_b) {
+    float r[24], p[24];
+    char *pb = B.p.data + rhs * B.p.rstride + b * B.p.bstride;
+    load24<SI>(B.r.data + rhs * B.r.rstride + b * B.r.bstride, B.r.scale_off, i, s, B.Ls, r);
+    load24<SI>(pb, B.p.scale_off, i, s, B.Ls, p);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) p[k] = r[k] + beta * p[k];
+    store24<SI>(pb, B.p.scale_off, i, s, B.Ls, p);
+  }
+  double tot;
+  if (group_reduce(0.0, B.partials + (size_t)grp * gridDim.x, gridDim.x, blockIdx.x,
+                   B.counters + grp, tot))
+    B.rr[grp] = B.rr_new[grp];
+}
+
+// z_glob = x (block layout -> global), with <r, z> summed over all blocks.
+__global__ void __launch_bounds__(kBlasThreads) blk_scatter_kernel(const BlockArgs B) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.z, b = blockIdx.y;
+  if (B.skip && B.skip[rhs]) return;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
+  double acc = 0.0;
+  if (i < B.n_b) {
+    const int h = B.gmap[(size_t)b * B.n_b + i];
+    float x[24], r[24];
+    load24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, i, s, B.Ls, x);
+    load24<F32>(B.rglob + rhs * B.grs, 0, h, s, B.Ls, r);
+    store24<F32>(B.zglob + rhs * B.grs, 0, h, s, B.Ls, x);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc += (double)r[k] * x[k];
+  }
+  acc = cta_sum(acc, red);
+  const int ntiles = gridDim.x * gridDim.y;
+  double tot;
+  if (group_reduce(acc, B.gpart + (size_t)rhs * ntiles, ntiles, b * gridDim.x + blockIdx.x,
+                   B.gcount + rhs, tot))
+    B.rz_out[(size_t)rhs * B.rz_rstride] = tot;
+}
+
+// out_glob = src (block layout -> FP32 global), used to read block vectors out.
+template <class SI>
+__global__ void __launch_bounds__(kBlasThreads) blk_export_kernel(const BlockArgs B,
+                                                                  const FieldRef src) {
+  const int rhs = blockIdx.z, b = blockIdx.y;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
+  if (i < B.n_b) {
+    const int h = B.gmap[(size_t)b * B.n_b + i];
+    float v[24];
+    load24<SI>(src.data + rhs * src.rstride + b * src.bstride, src.scale_off, i, s, B.Ls, v);
+    store24<F32>(B.zglob + rhs * B.grs, 0, h, s, B.Ls, v);
+  }
+}
+
+void block_export(dwf_prec in, const BlockArgs &B, const FieldRef &src, int nrhs,
+                  cudaStream_t st) {
+  dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
+  switch (in) {
+    case DWF_FP32: blk_export_kernel<F32><<<g, kBlasThreads, 0, st>>>(B, src); break;
+    case DWF_FP16: blk_export_kernel<F16><<<g, kBlasThreads, 0, st>>>(B, src); break;
+    case DWF_BF16: blk_export_kernel<BF16><<<g, kBlasThreads, 0, st>>>(B, src); break;
+    default: throw Error{DWF_ERR_UNSUPPORTED, "inner precision"};
+  }
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+#define DISPATCH_IN(in, KERNEL, ...)                                         \
+  do {                                                                       \
+    switch (in) {                                                            \
+      case DWF_FP32: KERNEL<F32 __VA_ARGS__><<<g, kBlasThreads, 0, st>>>(B); break; \
+      case DWF_FP16: KERNEL<F16 __VA_ARGS__><<<g, kBlasThreads, 0, st>>>(B); break; \
+      case DWF_BF16: KERNEL<BF16 __VA_ARGS__><<<g, kBlasThreads, 0, st>>>(B); break; \
+      default: throw Error{DWF_ERR_UNSUPPORTED, "inner precision"};          \
+    }                                                                        \
+    DWF_CUDA_TRY(cudaGetLastError());                                        \
+  } while (0)
+
+void block_gather(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st) {
+  dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
+  DISPATCH_IN(in, blk_gather_kernel, );
+}
+void block_xr(dwf_prec in, const BlockArgs &B, int last, int nrhs, cudaStream_t st) {
+  dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
+  if (last)
+    DISPATCH_IN(in, blk_xr_kernel, , true);
+  else
+    DISPATCH_IN(in, blk_xr_kernel, , false);
+}
+void block_p(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st) {
+  dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
+  DISPATCH_IN(in, blk_p_kernel, );
+}
+void block_scatter(const BlockArgs &B, int nrhs, cudaStream_t st) {
+  dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
+  blk_scatter_kernel<<<g, kBlasThreads, 0, st>>>(B);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace dwf

@@ -1,0 +1,61 @@
+// Arguments of the vector-update and reduction kernels (blas.cu).
+#pragma once
+
+#include "dwf_internal.cuh"
+
+namespace dwf {
+
+// Outer solve (Algorithm 1): flat views of native fields, one rhs after another.
+struct OuterArgs {
+  const char *b64 = nullptr;  // FP64 right-hand side
+  char *r64 = nullptr;        // FP64 residual
+  char *x64 = nullptr;        // FP64 solution accumulator
+  const char *Ax64 = nullptr; // FP64 A x for the reliable update
+  char *xlo = nullptr, *rlo = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr;
+  long long rs64 = 0, rslo = 0;  // bytes between right-hand sides
+  long long n4 = 0;              // groups of 4 reals per right-hand side
+  int Ls = 0;
+  OuterScalars *scal = nullptr;
+  double *partials = nullptr;    // [rhs][gridDim.x]
+  unsigned int *counters = nullptr;  // [rhs]
+  const int *skip = nullptr;
+  int plain = 0;                 // 1: z = r (no preconditioner)
+};
+
+// Inner block CG (k iterations on every block at once).
+struct BlockArgs {
+  FieldRef r, p, Ap;  // inner precision, block layout
+  FieldRef x;         // FP32, block layout
+  const char *rglob = nullptr;  // FP32 native global even field
+  char *zglob = nullptr;
+  long long grs = 0;            // global rhs stride
+  const int *gmap = nullptr;    // [nblocks][n_b] global half index
+  int n_b = 0, Ls = 0, nblocks = 0;
+  double *rr = nullptr, *rr_new = nullptr, *pAp = nullptr;  // [rhs][nblocks]
+  double *partials = nullptr;       // [rhs][nblocks][tiles]
+  unsigned int *counters = nullptr; // [rhs][nblocks]
+  double *gpart = nullptr;          // [rhs][nblocks * tiles]
+  unsigned int *gcount = nullptr;   // [rhs]
+  double *rz_out = nullptr;         // rz_out[rhs * rz_rstride]
+  int rz_rstride = 0;
+  const int *skip = nullptr;
+};
+
+void outer_init(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
+void outer_axpy_xr(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
+void outer_xpay_p(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
+void outer_copy_p(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
+void outer_promote(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
+void outer_ru_residual(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
+void outer_set_rz(const OuterArgs &A, int nrhs, cudaStream_t st);
+int outer_ctas();
+
+void block_gather(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st);
+void block_xr(dwf_prec in, const BlockArgs &B, int last, int nrhs, cudaStream_t st);
+void block_p(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st);
+void block_scatter(const BlockArgs &B, int nrhs, cudaStream_t st);
+void block_export(dwf_prec in, const BlockArgs &B, const FieldRef &src, int nrhs,
+                  cudaStream_t st);
+int block_tiles(int n_b, int Ls);
+
+}  // namespace dwf

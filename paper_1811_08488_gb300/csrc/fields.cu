@@ -1,0 +1,268 @@
+// Layout and precision conversions, gauge-link packing, and the standalone
+// Ls-direction operators M_5, M_5^-1 (paper Sec. 2.2 and eq. (dirac_equation)).
+#include <type_traits>
+
+#include "device_common.cuh"
+
+namespace dwf {
+
+// ---------------------------------------------------------------------------
+// Standalone Ls-direction operator: out = q0 (p0 + p1 S)[(1 - r S)^-1] in.
+// ---------------------------------------------------------------------------
+template <class S, bool DAG>
+__global__ void __launch_bounds__(256) ls_kernel(char *out, const char *in, long long rstride,
+                                                 long long soff, int nsite, int Ls, int inv,
+                                                 const __grid_constant__ HopParams P) {
+  using R = typename S::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rhs = blockIdx.z;
+  const int nsites = P.nsites;
+  const int tid = threadIdx.x, s = tid % Ls, sl = tid / Ls;
+  const int site = blockIdx.x * nsites + sl;
+  const bool active = sl < nsites && site < nsite;
+  const int col = Ls + 1;
+  R *T = reinterpret_cast<R *>(smem_raw);
+  const char *ip = in + rhs * rstride;
+  char *op = out + rhs * rstride;
+  if (active) {
+    R v[24];
+    load24<S>(ip, soff, site, s, Ls, v);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) T[(sl * 24 + k) * col + s] = v[k];
+  }
+  __syncthreads();
+  for (int w = tid; w < nsites * 24; w += blockDim.x) {
+    if (blockIdx.x * nsites + w / 24 >= nsite) continue;
+    const bool down = ((w % 24) < 12) != DAG;
+    ls_column<R>(T + w * col, nullptr, Ls, down, inv != 0, P.coef[rhs]);
+  }
+  __syncthreads();
+  if (active) {
+    R v[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) v[k] = T[(sl * 24 + k) * col + s];
+    store24<S>(op, soff, site, s, Ls, v);
+  }
+}
+
+void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride, int nsite, int Ls,
+                  int dagger, int inv, int nrhs, const LsCoef *coef, cudaStream_t st) {
+  HopParams P;
+  for (int r = 0; r < nrhs; ++r) P.coef[r] = coef[r];
+  const int nsites = hop_sites_per_cta(Ls, p);
+  P.nsites = nsites;
+  dim3 grid((nsite + nsites - 1) / nsites, 1, nrhs), block((nsites * Ls + 31) / 32 * 32);
+  const size_t smem = (size_t)nsites * 24 * (Ls + 1) * (p == DWF_FP64 ? 8 : 4);
+  const long long soff = (long long)align_up(field_data_bytes(p, nsite, Ls), 256);
+#define LSK(ST, D)                                                                          \
+  do {                                                                                      \
+    DWF_CUDA_TRY(cudaFuncSetAttribute(ls_kernel<ST, D>,                                     \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10)); \
+    ls_kernel<ST, D><<<grid, block, smem, st>>>(out, in, rstride, soff, nsite, Ls, inv, P); \
+  } while (0)
+  if (p == DWF_FP64) {
+    if (dagger) LSK(F64, true); else LSK(F64, false);
+  } else if (p == DWF_FP32) {
+    if (dagger) LSK(F32, true); else LSK(F32, false);
+  } else {
+    throw Error{DWF_ERR_UNSUPPORTED, "M_5 / M_5^-1 entry points take FP64 or FP32 fields"};
+  }
+#undef LSK
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Canonical <-> native. The canonical half field is [rhs][s][h][24 reals],
+// because the half index h = idx/2 runs over [t][z][y][xh].
+// ---------------------------------------------------------------------------
+template <class S, class C>
+__global__ void import_kernel(char *native, long long nstride, long long soff, const C *canon,
+                              int nsite, int Ls) {
+  const long long n = (long long)nsite * Ls;
+  const int rhs = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(i / Ls), s = (int)(i % Ls);
+    const C *src = canon + (((size_t)rhs * Ls + s) * nsite + h) * 24;
+    typename S::R v[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) v[k] = (typename S::R)src[k];
+    store24<S>(native + rhs * nstride, soff, h, s, Ls, v);
+  }
+}
+
+template <class S, class C>
+__global__ void export_kernel(C *canon, const char *native, long long nstride, long long soff,
+                              int nsite, int Ls) {
+  const long long n = (long long)nsite * Ls;
+  const int rhs = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(i / Ls), s = (int)(i % Ls);
+    C *dst = canon + (((size_t)rhs * Ls + s) * nsite + h) * 24;
+    typename S::R v[24];
+    load24<S>(native + rhs * nstride, soff, h, s, Ls, v);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) dst[k] = (C)v[k];
+  }
+}
+
+void launch_import(dwf_prec p, char *native, long long nstride, const void *canon, int canon_fp32,
+                   int nsite, int Ls, const int *, int nrhs, cudaStream_t st) {
+  const long long soff = (long long)align_up(field_data_bytes(p, nsite, Ls), 256);
+  dim3 grid(1024, nrhs), block(256);
+#define IMP(ST)                                                                          \
+  do {                                                                                   \
+    if (canon_fp32)                                                                      \
+      import_kernel<ST, float><<<grid, block, 0, st>>>(native, nstride, soff,            \
+                                                       (const float *)canon, nsite, Ls); \
+    else                                                                                 \
+      import_kernel<ST, double><<<grid, block, 0, st>>>(native, nstride, soff,           \
+                                                        (const double *)canon, nsite, Ls); \
+  } while (0)
+  switch (p) {
+    case DWF_FP64: IMP(F64); break;
+    case DWF_FP32: IMP(F32); break;
+    case DWF_FP16: IMP(F16); break;
+    case DWF_BF16: IMP(BF16); break;
+  }
+#undef IMP
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_export(dwf_prec p, void *canon, int canon_fp32, const char *native, long long nstride,
+                   int nsite, int Ls, const int *, int nrhs, cudaStream_t st) {
+  const long long soff = (long long)align_up(field_data_bytes(p, nsite, Ls), 256);
+  dim3 grid(1024, nrhs), block(256);
+#define EXP(ST)                                                                               \
+  do {                                                                                        \
+    if (canon_fp32)                                                                           \
+      export_kernel<ST, float><<<grid, block, 0, st>>>((float *)canon, native, nstride, soff, \
+                                                       nsite, Ls);                            \
+    else                                                                                      \
+      export_kernel<ST, double><<<grid, block, 0, st>>>((double *)canon, native, nstride,     \
+                                                        soff, nsite, Ls);                     \
+  } while (0)
+  switch (p) {
+    case DWF_FP64: EXP(F64); break;
+    case DWF_FP32: EXP(F32); break;
+    case DWF_FP16: EXP(F16); break;
+    case DWF_BF16: EXP(BF16); break;
+  }
+#undef EXP
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Gauge links. Input U[t][z][y][x][mu][3][3] complex128; output records
+// [owner][mu] with owner = parity * Vh + idx/2 (the combined numbering). The
+// link leaving t = Lt-1 carries the antiperiodic sign.
+// ---------------------------------------------------------------------------
+__global__ void pack_links_kernel(const double *U, double *l64, float *l32, __half *l16, int Lx,
+                                  int Ly, int Lz, int Lt, int tap) {
+  const int V4 = Lx * Ly * Lz * Lt, Vh = V4 / 2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V4 * 4; i += gridDim.x * blockDim.x) {
+    const int idx = i / 4, mu = i % 4;
+    const int x = idx % Lx, y = (idx / Lx) % Ly, z = (idx / (Lx * Ly)) % Lz,
+              t = idx / (Lx * Ly * Lz);
+    const int par = (x + y + z + t) & 1;
+    const int owner = par * Vh + (idx >> 1);
+    const double sgn = (tap && mu == 3 && t == Lt - 1) ? -1.0 : 1.0;
+    const double *src = U + (size_t)i * 18;
+    const size_t rec = (size_t)owner * 4 + mu;
+    for (int k = 0; k < 18; ++k) {
+      const double v = sgn * src[k];
+      l64[rec * 18 + k] = v;
+      l32[rec * 20 + k] = (float)v;
+      l16[rec * 24 + k] = __double2half(v);
+    }
+    l32[rec * 20 + 18] = 0.f;
+    l32[rec * 20 + 19] = 0.f;
+    for (int k = 18; k < 24; ++k) l16[rec * 24 + k] = __double2half(0.0);
+  }
+}
+
+void launch_pack_links(const double *U, char *l64, char *l32, char *l16, const int dims[4],
+                       int tap, cudaStream_t st) {
+  pack_links_kernel<<<1024, 256, 0, st>>>(U, (double *)l64, (float *)l32, (__half *)l16, dims[0],
+                                          dims[1], dims[2], dims[3], tap);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+// Per-block link copies: dst[block][c][mu] = record of global owner gowner[block][c]
+// (owner ids in the combined numbering parity * Vh + idx/2).
+__global__ void block_links_kernel(char *dst, const char *src, int words, const int *gowner,
+                                   long long nrec) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrec * words;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / words;
+    const int w = (int)(i % words);
+    const int owner = gowner[r / 4];
+    const int mu = (int)(r % 4);
+    const uint4 *s = reinterpret_cast<const uint4 *>(src) + ((size_t)owner * 4 + mu) * words + w;
+    reinterpret_cast<uint4 *>(dst)[r * words + w] = __ldg(s);
+  }
+}
+
+void launch_block_links(dwf_prec p, char *dst, const char *src_l32, const char *src_l16,
+                        const int *gowner, int n_comb, int nblocks, const int *,
+                        cudaStream_t st) {
+  const int rec = (int)link_record_bytes(p == DWF_FP32 ? DWF_FP32 : DWF_FP16);
+  const char *src = (p == DWF_FP32) ? src_l32 : src_l16;
+  block_links_kernel<<<1024, 256, 0, st>>>(dst, src, rec / 16, gowner,
+                                           (long long)nblocks * n_comb * 4);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients
+// ---------------------------------------------------------------------------
+static LsCoef base(double mf) {
+  LsCoef c{};
+  c.q0 = 1.0;
+  c.p0 = 1.0;
+  c.mf = mf;
+  c.pre_b = 1.0;
+  return c;
+}
+LsCoef coef_identity(double q0) {
+  LsCoef c = base(0.0);
+  c.q0 = q0;
+  return c;
+}
+LsCoef coef_m5(const dwf_action &a, double mf, double q0) {
+  LsCoef c = base(mf);
+  const double al = a.b * (4.0 - a.M5) + 1.0, be = a.c * (4.0 - a.M5) - 1.0;
+  c.q0 = q0;
+  c.p0 = al;
+  c.p1 = be;
+  return c;
+}
+static void set_inv(LsCoef &c, const dwf_action &a, double mf) {
+  const double al = a.b * (4.0 - a.M5) + 1.0, be = a.c * (4.0 - a.M5) - 1.0;
+  c.r = -be / al;
+  double rl = 1.0;
+  for (int k = 0; k < a.Ls; ++k) rl *= c.r;
+  c.inv_den = 1.0 / (1.0 + mf * rl);
+  c.q0 /= al;
+}
+LsCoef coef_m5inv(const dwf_action &a, double mf, double q0) {
+  LsCoef c = base(mf);
+  c.q0 = q0;
+  set_inv(c, a, mf);
+  return c;
+}
+LsCoef coef_mphi(const dwf_action &a, double mf, double q0) {
+  LsCoef c = base(mf);
+  c.q0 = q0;
+  c.p0 = a.b;
+  c.p1 = a.c;
+  return c;
+}
+LsCoef coef_k(const dwf_action &a, double mf, double q0) {
+  LsCoef c = coef_mphi(a, mf, q0);
+  set_inv(c, a, mf);
+  return c;
+}
+
+}  // namespace dwf

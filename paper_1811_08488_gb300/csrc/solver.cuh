@@ -1,0 +1,84 @@
+// Host-side composition of the operators and the solver plans.
+#pragma once
+
+#include "blas.cuh"
+#include "dwf_internal.cuh"
+
+namespace dwf {
+
+// Three half-field temporaries (odd u, even y, odd v) of one precision.
+struct OpWork {
+  char *u = nullptr, *y = nullptr, *v = nullptr;
+  long long rstride = 0;
+};
+
+// Optional fused reduction of Re<dotv, out> into dot_out (stage D of A).
+struct DotSpec {
+  const char *dotv = nullptr;
+  double *partials = nullptr;
+  unsigned int *counters = nullptr;
+  double *dot_out = nullptr;
+  int dot_rstride = 0;
+};
+
+FieldRef global_ref(const dwf_ctx *ctx, dwf_prec p, const void *ptr);
+const char *link_ptr(const dwf_ctx *ctx, dwf_prec p);
+OpWork op_work(dwf_ctx *ctx, dwf_prec p, int nrhs);
+
+void apply_dslash(dwf_ctx *ctx, void *out, const void *in, int out_parity, int dagger,
+                  dwf_prec p, int nrhs, const double *mf, cudaStream_t st);
+void apply_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
+               const double *mf, const OpWork &w, cudaStream_t st);
+void apply_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec p, int nrhs,
+                 const double *mf, const OpWork &w, const DotSpec *dot, const int *skip,
+                 cudaStream_t st);
+
+// The multisplitting block plan: geometry, tables, per-block links, vectors.
+struct BlockPlan {
+  BlockGeometry bg;
+  dwf_prec inner = DWF_FP16;
+  int nrhs = 0;
+  int Ls = 0;
+  DevBuf nbr_oe, nbr_eo, gmap_b, gowner;
+  DevBuf links;
+  long long link_bstride = 0;
+  DevBuf r, p, Ap, x, u1, y, u2;
+  FieldRef fr, fp, fAp, fx, fu1, fy, fu2;
+  DevBuf scal;  // rr, rr_new, pAp: 3 x [nrhs][nblocks] doubles
+  DevBuf partials, counters, gpart, gcount;
+  bool links_valid = false;
+};
+
+BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int nrhs,
+                          cudaStream_t st);
+// out = (+)_s A_s p on the plan's block vectors (p -> Ap), optional <p, Ap>.
+void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const double *mf,
+                   bool with_dot, const int *skip, cudaStream_t st);
+// z = M^-1 r on FP32 global fields; <r, z> -> rz_out[rhs * rz_rstride] if given.
+void block_precondition(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, int k, int snake,
+                        int nrhs, const double *mf, double *rz_out, int rz_rstride,
+                        const int *skip, cudaStream_t st);
+
+BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double *rz_out,
+                     int rz_rstride, const int *skip);
+
+struct SolverPlan {
+  dwf_prec lo = DWF_FP32;
+  int nrhs = 0;
+  DevBuf b64, x64, r64, Ax64;
+  DevBuf xlo, rlo, p, Ap, z;
+  DevBuf wlo, w64;  // operator temporaries
+  DevBuf scal, partials, counters, opart, ocount, skip_iter, skip_ru;
+  OuterScalars *host_scal = nullptr;
+  int *host_skip = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::string graph_key;
+  ~SolverPlan();
+};
+
+dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
+                 const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st);
+
+void prepare_kernels();
+
+}  // namespace dwf

@@ -1,0 +1,137 @@
+"""GPU solver parity: mspcg_solve through the C ABI, checked by the FP64 oracle.
+
+Every solve must reach a true residual |b - A x| / |b| <= 1e-10 recomputed by
+the oracle in FP64, and match the oracle's own solution to within the
+condition-number bound kappa * 1e-10 (estimated from the oracle's CG).
+"""
+import numpy as np
+import pytest
+
+from oracle import dwf_operator as op
+from oracle import solvers as sv
+from paper_1811_08488_gb300 import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dwf():
+    from paper_1811_08488_gb300 import dwf as d
+    return d
+
+
+def setup(dims, Ls, b, c, eps, seed, M5=1.8):
+    act = op.Action(dims=tuple(dims), Ls=Ls, M5=M5, b=b, c=c)
+    Uc = syn.gauge_field(dims, eps, seed)
+    ctx = dwf().Context(dims, Ls, b=b, c=c, M5=M5)
+    ctx.gauge_load(Uc)
+    return act, Uc, op.gauge_to_mu_major(Uc), ctx
+
+
+def oracle_resid(act, U, x_half, b_half, mf):
+    xf = op.half_to_full(x_half, 0)
+    bf = op.half_to_full(b_half, 0)
+    r = bf - op.mdagm(act, U, xf, mf)
+    return np.sqrt(op.norm2(r) / op.norm2(bf))
+
+
+def run(ctx, srcs, masses, **kw):
+    b = torch.from_numpy(np.ascontiguousarray(np.stack(srcs))).cuda()
+    x = torch.zeros_like(b)
+    prm = dwf().default_params(**kw)
+    st, info = ctx.solve(x, b, masses, prm)
+    return st, info, [a for a in x.cpu().numpy()]
+
+
+def test_plain_cg_fp64_shamir():
+    """Plain even-odd CG in FP64 (the Shamir 8^4 x 8 workload at a smaller volume)."""
+    act, Uc, U, ctx = setup((4, 4, 4, 8), 8, 1.0, 0.0, 0.3, 1000)
+    src = syn.half_field(act.dims, act.Ls, 2000)
+    st, info, x = run(ctx, [src], [0.1], inner_iters=0, outer=dwf().DWF_FP64, tol=1e-10)
+    assert st == 0 and info[0]["converged"]
+    assert oracle_resid(act, U, x[0], src, 0.1) <= 1e-10
+    xo, it, _ = sv.cg(lambda v: op.mdagm(act, U, v, 0.1), op.half_to_full(src, 0), 1e-10)
+    rel = np.abs(x[0] - op.full_to_half(xo, 0)).max() / np.abs(xo).max()
+    assert rel < 1e-8
+    # FP64 CG takes the oracle's iteration count (the host checks convergence
+    # between launches, so it may run a few iterations past it)
+    assert it <= info[0]["outer_iters"] <= it + 10
+
+
+@pytest.mark.parametrize("inner", ["fp32", "fp16", "bf16"])
+def test_mspcg_mixed_precision(inner):
+    act, Uc, U, ctx = setup((8, 8, 8, 8), 8, 1.5, 0.5, 0.4, 1001)
+    mf = 0.02
+    src = syn.half_field(act.dims, act.Ls, 2001)
+    st, info, x = run(ctx, [src], [mf], inner_iters=0, tol=1e-10)
+    assert st == 0
+    plain_iters = info[0]["outer_iters"]
+    assert oracle_resid(act, U, x[0], src, mf) <= 1e-10
+    st, info, x2 = run(ctx, [src], [mf], inner_iters=6, block=(4, 4, 4, 4), inner=inner, tol=1e-10)
+    assert st == 0 and info[0]["converged"], info
+    assert oracle_resid(act, U, x2[0], src, mf) <= 1e-10
+    assert info[0]["outer_iters"] < plain_iters
+    # same solution within kappa * tol
+    rel = np.linalg.norm(x2[0] - x[0]) / np.linalg.norm(x[0])
+    assert rel < 1e-6
+
+
+def test_multi_rhs_uneven_masses():
+    """Several right-hand sides with different masses in one call; each stops
+    on its own (per-rhs early exit)."""
+    act, Uc, U, ctx = setup((4, 4, 8, 8), 6, 1.5, 0.5, 0.4, 1003)
+    masses = [0.005, 0.02, 0.1, 0.4]
+    srcs = [syn.half_field(act.dims, act.Ls, 2003 + r) for r in range(4)]
+    st, info, x = run(ctx, srcs, masses, inner_iters=4, block=(4, 4, 4, 4), inner="fp16")
+    assert st == 0
+    its = [i["outer_iters"] for i in info]
+    assert its[0] > its[-1]  # lighter mass, more iterations
+    for r in range(4):
+        assert info[r]["converged"]
+        assert oracle_resid(act, U, x[r], srcs[r], masses[r]) <= 1e-10
+
+
+def test_snake_terms_matter_on_gpu():
+    act, Uc, U, ctx = setup((8, 8, 8, 8), 8, 1.5, 0.5, 0.45, 1004)
+    src = syn.half_field(act.dims, act.Ls, 2004)
+    _, i_snake, _ = run(ctx, [src], [0.01], inner_iters=4, block=(4, 4, 4, 4), snake=1)
+    _, i_trunc, _ = run(ctx, [src], [0.01], inner_iters=4, block=(4, 4, 4, 4), snake=0)
+    assert i_snake[0]["outer_iters"] < i_trunc[0]["outer_iters"]
+
+
+def test_host_buffers():
+    act, Uc, U, ctx = setup((4, 4, 4, 8), 4, 1.5, 0.5, 0.4, 1005)
+    src = np.ascontiguousarray(syn.half_field(act.dims, act.Ls, 2005)[None])
+    x = np.zeros_like(src)
+    prm = dwf().default_params(inner_iters=3, block=(4, 4, 4, 4), io_on_host=1)
+    st, info = ctx.solve(x, src, [0.05], prm)
+    assert st == 0
+    assert oracle_resid(act, U, x[0], src[0], 0.05) <= 1e-10
+
+
+def test_error_codes():
+    d = dwf()
+    act, Uc, U, ctx = setup((4, 4, 4, 4), 4, 1.5, 0.5, 0.4, 1006)
+    src = syn.half_field(act.dims, act.Ls, 2006)
+    # not converged within maxiter: x and info still filled
+    st, info, x = run(ctx, [src], [0.01], inner_iters=0, maxiter=3)
+    assert st == 4 and info[0]["converged"] == 0 and info[0]["outer_iters"] == 3
+    assert info[0]["true_resid"] > 1e-10
+    # bad block
+    with pytest.raises(d.DwfError) as e:
+        run(ctx, [src], [0.01], inner_iters=2, block=(3, 4, 4, 4))
+    assert e.value.code == 1
+    # operator before gauge load
+    ctx2 = d.Context((4, 4, 4, 4), 4)
+    f = ctx2.new_field("fp32")
+    g = ctx2.new_field("fp32")
+    with pytest.raises(d.DwfError) as e:
+        ctx2.dslash_eo(g, f, 0, 0, "fp32", 0.1)
+    assert e.value.code == 7
+    # invalid action
+    with pytest.raises(d.DwfError) as e:
+        d.Context((4, 5, 4, 4), 4)
+    assert e.value.code == 1
+    # zero source: x = 0, converged at once
+    st, info, x = run(ctx, [np.zeros_like(src)], [0.01], inner_iters=2, block=(4, 4, 4, 4))
+    assert st == 0 and info[0]["converged"] and np.all(x[0] == 0)
