@@ -194,6 +194,26 @@ dwf_status dwf_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger,
 dwf_status dwf_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec,
                      int nrhs, const double *mf, void *stream);
 
+/* Size of the library's fixed device scratch array used by dwf_mdagm_noalloc. */
+#define DWF_NOALLOC_SCRATCH_BYTES (24u << 20)
+
+/* out = D_PC^+ D_PC in, exactly as dwf_mdagm, but without allocating device
+ * memory. The paper has no counterpart: this is an interface for callers that
+ * cannot call cudaMalloc -- applications whose own pool allocator already owns
+ * the device memory, and host loops that must not take cudaMalloc's implicit
+ * device synchronisation. The three half-field temporaries live in one
+ * file-scope device array of DWF_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * loading the library holds until exit; the call needs
+ * 3 * dwf_field_bytes(ctx, prec, 1) * nrhs bytes of it and returns INVALID_ARG
+ * (with a message) when that exceeds the array. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture. All calls share the array and leave their
+ * temporaries in it (nothing in it needs to start at zero); calls whose GPU
+ * work overlaps race on it, so the caller must serialise them.
+ * prec: DWF_FP64 or DWF_FP32. Errors: INVALID_ARG, NO_GAUGE, CUDA. */
+dwf_status dwf_mdagm_noalloc(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec,
+                             int nrhs, const double *mf, void *stream);
+
 /* Block operator of the multisplitting (paper Sec. 2.3): out = (+)_s A_s in,
  * A_s = P_s D_PC^+ D_PC P_s (snake = 1) or the per-hop Dirichlet operator
  * (snake = 0), on the blocks of params->block, computed in params->inner

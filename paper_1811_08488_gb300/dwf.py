@@ -23,11 +23,13 @@ PREC = {"fp64": DWF_FP64, "fp32": DWF_FP32, "fp16": DWF_FP16, "bf16": DWF_BF16}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NOT_CONVERGED",
           5: "TIMEOUT", 6: "NAN", 7: "NO_GAUGE"}
 MAX_RHS = 16
+NOALLOC_SCRATCH_BYTES = 24 << 20
 
 # Every symbol include/dwf.h declares.
 EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_default",
            "dwf_gauge_load", "dwf_field_bytes", "dwf_field_import", "dwf_field_export",
-           "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_mpc", "dwf_mdagm", "dwf_block_apply",
+           "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_mpc", "dwf_mdagm", "dwf_mdagm_noalloc",
+           "dwf_block_apply",
            "dwf_block_precond", "mspcg_solve"]
 
 
@@ -77,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_m5inv": (I, [P, P, P, I, I, I, D, P]),
         "dwf_mpc": (I, [P, P, P, I, I, I, D, P]),
         "dwf_mdagm": (I, [P, P, P, I, I, D, P]),
+        "dwf_mdagm_noalloc": (I, [P, P, P, I, I, D, P]),
         "dwf_block_apply": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "dwf_block_precond": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "mspcg_solve": (I, [P, P, P, I, D, C.POINTER(SolverParams), C.POINTER(SolveInfo), P]),
@@ -224,6 +227,13 @@ class Context:
         m, mp = _masses(mf)
         self._check(lib().dwf_mdagm(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
                                     PREC.get(prec, prec), m.size, mp, _stream(stream)))
+
+    def mdagm_noalloc(self, out, inp, prec, mf, stream=None):
+        """D_PC^+ D_PC without device allocation (temporaries in the library's
+        fixed scratch array of NOALLOC_SCRATCH_BYTES)."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_mdagm_noalloc(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
+                                            PREC.get(prec, prec), m.size, mp, _stream(stream)))
 
     def block_apply(self, out, inp, params, mf, stream=None):
         m, mp = _masses(mf)
