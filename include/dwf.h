@@ -40,11 +40,11 @@
  * Native half field (all operator entry points): one right-hand side after
  * another, each dwf_field_bytes(ctx, prec, 1) bytes (a multiple of 256).
  * Inside one right-hand side, the 24 reals of (site h, s) -- ordered
- * [spin][colour][re,im] -- are cut into 16-byte chunks, and chunk k of all Ls
- * slices of a site is contiguous:
- *     DWF_FP64: 12 chunks of 2 doubles,  byte offset ((h*12 + k)*Ls + s)*16
- *     DWF_FP32:  6 chunks of 4 floats,   byte offset ((h*6  + k)*Ls + s)*16
- *     DWF_FP16/BF16: 3 chunks of 8 halves, byte offset ((h*3 + k)*Ls + s)*16,
+ * [spin][colour][re,im] -- are cut into 16-byte chunks, and chunk k is stored
+ * for all (h, s) before chunk k+1 (chunk-major, s fastest), V = Vh = V4/2:
+ *     DWF_FP64: 12 chunks of 2 doubles,  byte offset ((k*V + h)*Ls + s)*16
+ *     DWF_FP32:  6 chunks of 4 floats,   byte offset ((k*V + h)*Ls + s)*16
+ *     DWF_FP16/BF16: 3 chunks of 8 halves, byte offset ((k*V + h)*Ls + s)*16,
  *         followed (at the next 256-byte boundary) by one float scale per
  *         (h, s) at [h*Ls + s]; the stored value times the scale is the field.
  * Convert with dwf_field_import / dwf_field_export.

@@ -16,49 +16,77 @@ constexpr int kOuterCtas = 152 * 4;
 constexpr int kBlasThreads = 256;
 int outer_ctas() { return kOuterCtas; }
 
-// Group i of a native field: the 4 reals [4c, 4c+4) of (site, s), numbered in
-// FP32 chunk order, i = (site * 6 + c) * Ls + s. In an FP32 field this is the
-// float4 at index i; in an FP64 field it is the two double2 chunks 2c and
-// 2c+1 of (site, s). Kernels that mix precisions therefore meet the same
-// (site, s, component) on both sides.
-template <class S>
-__device__ __forceinline__ void ld4(const char *p, long long i, int Ls, double v[4]) {
+// Group i of a native field: the 4 reals [4c, 4c+4) of element e = site*Ls + s,
+// numbered in FP32 order i = c * cs + e (cs = nsite * Ls, chunk-major). In an
+// FP32 field this is the float4 at index i; in an FP64 field it is the double2
+// chunks 2c and 2c+1 of e, at (2c) * cs + e and (2c + 1) * cs + e. Kernels that
+// mix precisions therefore meet the same (site, s, component) on both sides.
+template <class S, class U>
+__device__ __forceinline__ void ld4(const char *p, long long i, long long cs, U v[4]) {
   if constexpr (std::is_same<S, F32>::value) {
     float4 q = reinterpret_cast<const float4 *>(p)[i];
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    v[0] = (U)q.x; v[1] = (U)q.y; v[2] = (U)q.z; v[3] = (U)q.w;
   } else {
-    const long long site = i / (6 * Ls);
-    const int rem = (int)(i - site * 6 * Ls), c = rem / Ls, s = rem - c * Ls;
-    const long long j = (site * 12 + 2 * c) * Ls + s;
+    const long long c = i / cs, e = i - c * cs;
+    const long long j = 2 * c * cs + e;
     double2 a = reinterpret_cast<const double2 *>(p)[j];
-    double2 b = reinterpret_cast<const double2 *>(p)[j + Ls];
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    double2 b = reinterpret_cast<const double2 *>(p)[j + cs];
+    v[0] = (U)a.x; v[1] = (U)a.y; v[2] = (U)b.x; v[3] = (U)b.y;
   }
 }
-template <class S>
-__device__ __forceinline__ void st4(char *p, long long i, int Ls, const double v[4]) {
+template <class S, class U>
+__device__ __forceinline__ void st4(char *p, long long i, long long cs, const U v[4]) {
   if constexpr (std::is_same<S, F32>::value) {
     reinterpret_cast<float4 *>(p)[i] =
         make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
   } else {
-    const long long site = i / (6 * Ls);
-    const int rem = (int)(i - site * 6 * Ls), c = rem / Ls, s = rem - c * Ls;
-    const long long j = (site * 12 + 2 * c) * Ls + s;
-    reinterpret_cast<double2 *>(p)[j] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2 *>(p)[j + Ls] = make_double2(v[2], v[3]);
+    const long long c = i / cs, e = i - c * cs;
+    const long long j = 2 * c * cs + e;
+    reinterpret_cast<double2 *>(p)[j] = make_double2((double)v[0], (double)v[1]);
+    reinterpret_cast<double2 *>(p)[j + cs] = make_double2((double)v[2], (double)v[3]);
   }
 }
-template <class S>
-__device__ __forceinline__ void round4(double v[4]) {
-  if constexpr (std::is_same<S, F32>::value) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (double)(float)v[k];
-  }
+// num / den (0 when den == 0), computed in FP64 by one thread of the CTA and
+// shared: FP64 division per thread would run on GB300's small FP64 pipe.
+template <class R>
+__device__ __forceinline__ R cta_ratio(double num, double den, double *out_d = nullptr) {
+  __shared__ double s_ratio;
+  if (threadIdx.x == 0) s_ratio = den != 0.0 ? num / den : 0.0;
+  __syncthreads();
+  if (out_d) *out_d = s_ratio;
+  return (R)s_ratio;
 }
 
 #define FLAT_LOOP(n4)                                                              \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n4); \
        i += (long long)gridDim.x * blockDim.x)
+
+// Per-thread sums: compensated (Kahan) in FP32 for FP32 fields, plain FP64 for
+// FP64 fields; the cross-thread and cross-CTA sums are FP64. FP64 arithmetic
+// per element would run on GB300's small FP64 pipe and make these
+// bandwidth-bound kernels compute-bound.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+struct SumD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <class SL> struct Acc { using T = KahanF; using R = float; };
+template <> struct Acc<F64> { using T = SumD; using R = double; };
+
+template <class R>
+__device__ __forceinline__ R sq4(const R v[4]) {
+  return v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+}
 
 // ---------------------------------------------------------------------------
 // Outer solve
@@ -73,10 +101,10 @@ __global__ void __launch_bounds__(kBlasThreads) init_kernel(const OuterArgs A) {
   double acc = 0.0;
   FLAT_LOOP(A.n4) {
     double v[4];
-    ld4<F64>(A.b64 + o64, i, A.Ls, v);
-    st4<F64>(A.r64 + o64, i, A.Ls, v);
-    st4<SL>(A.rlo + olo, i, A.Ls, v);
-    acc += v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+    ld4<F64>(A.b64 + o64, i, A.cs, v);
+    st4<F64>(A.r64 + o64, i, A.cs, v);
+    st4<SL>(A.rlo + olo, i, A.cs, v);
+    acc += sq4(v);
   }
   acc = cta_sum(acc, red);
   double tot;
@@ -93,36 +121,36 @@ __global__ void __launch_bounds__(kBlasThreads) init_kernel(const OuterArgs A) {
 // x += alpha p; r -= alpha Ap; |r|^2 with alpha = <r,z> / <p,Ap> (Algorithm 1).
 template <class SL>
 __global__ void __launch_bounds__(kBlasThreads) axpy_xr_kernel(const OuterArgs A) {
+  using R = typename Acc<SL>::R;
   __shared__ double red[32];
   const int rhs = blockIdx.y;
   if (A.skip && A.skip[rhs]) return;
   OuterScalars *sc = A.scal + rhs;
-  const double pAp = sc->pAp;
-  const double alpha = pAp != 0.0 ? sc->rz / pAp : 0.0;
+  double alpha_d;
+  const R alpha = cta_ratio<R>(sc->rz, sc->pAp, &alpha_d);
   const long long o = rhs * A.rslo;
-  double acc = 0.0;
+  typename Acc<SL>::T acc;
   FLAT_LOOP(A.n4) {
-    double x[4], r[4], p[4], q[4];
-    ld4<SL>(A.xlo + o, i, A.Ls, x);
-    ld4<SL>(A.rlo + o, i, A.Ls, r);
-    ld4<SL>(A.p + o, i, A.Ls, p);
-    ld4<SL>(A.Ap + o, i, A.Ls, q);
+    R x[4], r[4], p[4], q[4];
+    ld4<SL>(A.xlo + o, i, A.cs, x);
+    ld4<SL>(A.rlo + o, i, A.cs, r);
+    ld4<SL>(A.p + o, i, A.cs, p);
+    ld4<SL>(A.Ap + o, i, A.cs, q);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       x[k] += alpha * p[k];
       r[k] -= alpha * q[k];
     }
-    st4<SL>(A.xlo + o, i, A.Ls, x);
-    st4<SL>(A.rlo + o, i, A.Ls, r);
-    round4<SL>(r);
-    acc += r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+    st4<SL>(A.xlo + o, i, A.cs, x);
+    st4<SL>(A.rlo + o, i, A.cs, r);
+    acc.add(sq4(r));
   }
-  acc = cta_sum(acc, red);
+  const double a = cta_sum(acc.value(), red);
   double tot;
-  if (group_reduce(acc, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
+  if (group_reduce(a, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
                    A.counters + rhs, tot)) {
     sc->rr = tot;
-    sc->alpha = alpha;
+    sc->alpha = alpha_d;
     sc->hist_rr[sc->iter % kHistory] = tot;
     if (A.plain) sc->rz_new = tot;
   }
@@ -131,43 +159,44 @@ __global__ void __launch_bounds__(kBlasThreads) axpy_xr_kernel(const OuterArgs A
 // beta = <r',z'> / <r,z>; p = z + beta p (z = r for plain CG); iter++.
 template <class SL>
 __global__ void __launch_bounds__(kBlasThreads) xpay_p_kernel(const OuterArgs A) {
-  __shared__ double red[32];
+  using R = typename Acc<SL>::R;
   const int rhs = blockIdx.y;
   if (A.skip && A.skip[rhs]) return;
   OuterScalars *sc = A.scal + rhs;
-  const double rz = sc->rz, rzn = sc->rz_new;
-  const double beta = rz != 0.0 ? rzn / rz : 0.0;
+  const double rzn = sc->rz_new;
+  double beta_d;
+  const R beta = cta_ratio<R>(rzn, sc->rz, &beta_d);
   const long long o = rhs * A.rslo;
   const char *z = A.plain ? A.rlo : A.z;
   FLAT_LOOP(A.n4) {
-    double p[4], zz[4];
-    ld4<SL>(A.p + o, i, A.Ls, p);
-    ld4<SL>(z + o, i, A.Ls, zz);
+    R p[4], zz[4];
+    ld4<SL>(A.p + o, i, A.cs, p);
+    ld4<SL>(z + o, i, A.cs, zz);
 #pragma unroll
     for (int k = 0; k < 4; ++k) p[k] = zz[k] + beta * p[k];
-    st4<SL>(A.p + o, i, A.Ls, p);
+    st4<SL>(A.p + o, i, A.cs, p);
   }
   double tot;
   if (group_reduce(0.0, A.partials + (size_t)rhs * gridDim.x, gridDim.x, blockIdx.x,
                    A.counters + rhs, tot)) {
     sc->rz = rzn;
-    sc->beta = beta;
+    sc->beta = beta_d;
     sc->iter += 1;
   }
-  (void)red;
 }
 
 // p = z (or r for plain CG).
 template <class SL>
 __global__ void __launch_bounds__(kBlasThreads) copy_p_kernel(const OuterArgs A) {
+  using R = typename Acc<SL>::R;
   const int rhs = blockIdx.y;
   if (A.skip && A.skip[rhs]) return;
   const long long o = rhs * A.rslo;
   const char *z = A.plain ? A.rlo : A.z;
   FLAT_LOOP(A.n4) {
-    double v[4];
-    ld4<SL>(z + o, i, A.Ls, v);
-    st4<SL>(A.p + o, i, A.Ls, v);
+    R v[4];
+    ld4<SL>(z + o, i, A.cs, v);
+    st4<SL>(A.p + o, i, A.cs, v);
   }
 }
 
@@ -179,13 +208,13 @@ __global__ void __launch_bounds__(kBlasThreads) promote_kernel(const OuterArgs A
   const long long o64 = rhs * A.rs64, olo = rhs * A.rslo;
   FLAT_LOOP(A.n4) {
     double x[4], d[4];
-    ld4<F64>(A.x64 + o64, i, A.Ls, x);
-    ld4<SL>(A.xlo + olo, i, A.Ls, d);
+    ld4<F64>(A.x64 + o64, i, A.cs, x);
+    ld4<SL>(A.xlo + olo, i, A.cs, d);
 #pragma unroll
     for (int k = 0; k < 4; ++k) x[k] += d[k];
-    st4<F64>(A.x64 + o64, i, A.Ls, x);
+    st4<F64>(A.x64 + o64, i, A.cs, x);
     const double z[4] = {0, 0, 0, 0};
-    st4<SL>(A.xlo + olo, i, A.Ls, z);
+    st4<SL>(A.xlo + olo, i, A.cs, z);
   }
 }
 
@@ -199,13 +228,13 @@ __global__ void __launch_bounds__(kBlasThreads) ru_residual_kernel(const OuterAr
   double acc = 0.0;
   FLAT_LOOP(A.n4) {
     double b[4], ax[4];
-    ld4<F64>(A.b64 + o64, i, A.Ls, b);
-    ld4<F64>(A.Ax64 + o64, i, A.Ls, ax);
+    ld4<F64>(A.b64 + o64, i, A.cs, b);
+    ld4<F64>(A.Ax64 + o64, i, A.cs, ax);
 #pragma unroll
     for (int k = 0; k < 4; ++k) b[k] -= ax[k];
-    st4<F64>(A.r64 + o64, i, A.Ls, b);
-    st4<SL>(A.rlo + olo, i, A.Ls, b);
-    acc += b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+    st4<F64>(A.r64 + o64, i, A.cs, b);
+    st4<SL>(A.rlo + olo, i, A.cs, b);
+    acc += sq4(b);
   }
   acc = cta_sum(acc, red);
   double tot;
@@ -273,16 +302,19 @@ __global__ void __launch_bounds__(kBlasThreads) blk_gather_kernel(const BlockArg
   if (i < B.n_b) {
     const int h = B.gmap[(size_t)b * B.n_b + i];
     float v[24];
-    load24<F32>(B.rglob + rhs * B.grs, 0, h, s, B.Ls, v);
+    load24<F32>(B.rglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, v);
+    float part = 0.f;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) acc += (double)v[k] * v[k];
+    for (int k = 0; k < 24; ++k) part += v[k] * v[k];
+    acc = part;
     const long long off = rhs * B.r.rstride + b * B.r.bstride;
-    store24<SI>(B.r.data + off, B.r.scale_off, i, s, B.Ls, v);
-    store24<SI>(B.p.data + rhs * B.p.rstride + b * B.p.bstride, B.p.scale_off, i, s, B.Ls, v);
+    store24<SI>(B.r.data + off, B.r.scale_off, B.r.cs, i * B.Ls + s, v);
+    store24<SI>(B.p.data + rhs * B.p.rstride + b * B.p.bstride, B.p.scale_off, B.p.cs, i * B.Ls + s,
+                v);
     float zero[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) zero[k] = 0.f;
-    store24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, i, s, B.Ls, zero);
+    store24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, B.x.cs, i * B.Ls + s, zero);
   }
   acc = cta_sum(acc, red);
   const int grp = rhs * B.nblocks + b;
@@ -299,31 +331,33 @@ __global__ void __launch_bounds__(kBlasThreads) blk_xr_kernel(const BlockArgs B)
   const int rhs = blockIdx.z, b = blockIdx.y;
   if (B.skip && B.skip[rhs]) return;
   const int grp = rhs * B.nblocks + b;
-  const double pAp = B.pAp[grp];
-  const float alpha = (float)(pAp != 0.0 ? B.rr[grp] / pAp : 0.0);
+  const float alpha = cta_ratio<float>(B.rr[grp], B.pAp[grp]);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
   double acc = 0.0;
   if (i < B.n_b) {
     float x[24], p[24];
     char *xb = B.x.data + rhs * B.x.rstride + b * B.x.bstride;
-    load24<F32>(xb, 0, i, s, B.Ls, x);
-    load24<SI>(B.p.data + rhs * B.p.rstride + b * B.p.bstride, B.p.scale_off, i, s, B.Ls, p);
+    load24<F32>(xb, 0, B.x.cs, i * B.Ls + s, x);
+    load24<SI>(B.p.data + rhs * B.p.rstride + b * B.p.bstride, B.p.scale_off, B.p.cs, i * B.Ls + s,
+               p);
 #pragma unroll
     for (int k = 0; k < 24; ++k) x[k] += alpha * p[k];
-    store24<F32>(xb, 0, i, s, B.Ls, x);
+    store24<F32>(xb, 0, B.x.cs, i * B.Ls + s, x);
     if (!LAST) {
       float r[24], q[24];
       char *rb = B.r.data + rhs * B.r.rstride + b * B.r.bstride;
-      load24<SI>(rb, B.r.scale_off, i, s, B.Ls, r);
-      load24<SI>(B.Ap.data + rhs * B.Ap.rstride + b * B.Ap.bstride, B.Ap.scale_off, i, s, B.Ls,
-                 q);
+      load24<SI>(rb, B.r.scale_off, B.r.cs, i * B.Ls + s, r);
+      load24<SI>(B.Ap.data + rhs * B.Ap.rstride + b * B.Ap.bstride, B.Ap.scale_off, B.Ap.cs,
+                 i * B.Ls + s, q);
+      float part = 0.f;
 #pragma unroll
       for (int k = 0; k < 24; ++k) {
         r[k] -= alpha * q[k];
-        acc += (double)r[k] * r[k];
+        part += r[k] * r[k];
       }
-      store24<SI>(rb, B.r.scale_off, i, s, B.Ls, r);
+      acc = part;
+      store24<SI>(rb, B.r.scale_off, B.r.cs, i * B.Ls + s, r);
     }
   }
   if (!LAST) {
@@ -341,18 +375,18 @@ __global__ void __launch_bounds__(kBlasThreads) blk_p_kernel(const BlockArgs B) 
   const int rhs = blockIdx.z, b = blockIdx.y;
   if (B.skip && B.skip[rhs]) return;
   const int grp = rhs * B.nblocks + b;
-  const double rr = B.rr[grp];
-  const float beta = (float)(rr != 0.0 ? B.rr_new[grp] / rr : 0.0);
+  const float beta = cta_ratio<float>(B.rr_new[grp], B.rr[grp]);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
   if (i < B.n_b) {
     float r[24], p[24];
     char *pb = B.p.data + rhs * B.p.rstride + b * B.p.bstride;
-    load24<SI>(B.r.data + rhs * B.r.rstride + b * B.r.bstride, B.r.scale_off, i, s, B.Ls, r);
-    load24<SI>(pb, B.p.scale_off, i, s, B.Ls, p);
+    load24<SI>(B.r.data + rhs * B.r.rstride + b * B.r.bstride, B.r.scale_off, B.r.cs, i * B.Ls + s,
+               r);
+    load24<SI>(pb, B.p.scale_off, B.p.cs, i * B.Ls + s, p);
 #pragma unroll
     for (int k = 0; k < 24; ++k) p[k] = r[k] + beta * p[k];
-    store24<SI>(pb, B.p.scale_off, i, s, B.Ls, p);
+    store24<SI>(pb, B.p.scale_off, B.p.cs, i * B.Ls + s, p);
   }
   double tot;
   if (group_reduce(0.0, B.partials + (size_t)grp * gridDim.x, gridDim.x, blockIdx.x,
@@ -371,11 +405,13 @@ __global__ void __launch_bounds__(kBlasThreads) blk_scatter_kernel(const BlockAr
   if (i < B.n_b) {
     const int h = B.gmap[(size_t)b * B.n_b + i];
     float x[24], r[24];
-    load24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, i, s, B.Ls, x);
-    load24<F32>(B.rglob + rhs * B.grs, 0, h, s, B.Ls, r);
-    store24<F32>(B.zglob + rhs * B.grs, 0, h, s, B.Ls, x);
+    load24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, B.x.cs, i * B.Ls + s, x);
+    load24<F32>(B.rglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, r);
+    store24<F32>(B.zglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, x);
+    float part = 0.f;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) acc += (double)r[k] * x[k];
+    for (int k = 0; k < 24; ++k) part += r[k] * x[k];
+    acc = part;
   }
   acc = cta_sum(acc, red);
   const int ntiles = gridDim.x * gridDim.y;
@@ -395,8 +431,9 @@ __global__ void __launch_bounds__(kBlasThreads) blk_export_kernel(const BlockArg
   if (i < B.n_b) {
     const int h = B.gmap[(size_t)b * B.n_b + i];
     float v[24];
-    load24<SI>(src.data + rhs * src.rstride + b * src.bstride, src.scale_off, i, s, B.Ls, v);
-    store24<F32>(B.zglob + rhs * B.grs, 0, h, s, B.Ls, v);
+    load24<SI>(src.data + rhs * src.rstride + b * src.bstride, src.scale_off, src.cs,
+               i * B.Ls + s, v);
+    store24<F32>(B.zglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, v);
   }
 }
 

@@ -14,7 +14,7 @@ struct OuterArgs {
   char *xlo = nullptr, *rlo = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr;
   long long rs64 = 0, rslo = 0;  // bytes between right-hand sides
   long long n4 = 0;              // groups of 4 reals per right-hand side
-  int Ls = 0;
+  long long cs = 0;              // elements per chunk plane: Vh * Ls
   OuterScalars *scal = nullptr;
   double *partials = nullptr;    // [rhs][gridDim.x]
   unsigned int *counters = nullptr;  // [rhs]
@@ -29,6 +29,7 @@ struct BlockArgs {
   const char *rglob = nullptr;  // FP32 native global even field
   char *zglob = nullptr;
   long long grs = 0;            // global rhs stride
+  int gcs = 0;                  // global elements per chunk plane: Vh * Ls
   const int *gmap = nullptr;    // [nblocks][n_b] global half index
   int n_b = 0, Ls = 0, nblocks = 0;
   double *rr = nullptr, *rr_new = nullptr, *pAp = nullptr;  // [rhs][nblocks]

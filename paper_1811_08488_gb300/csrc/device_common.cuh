@@ -44,127 +44,212 @@ __device__ __forceinline__ uint4 pack8(const float *v, float scl) {
   return q;
 }
 
-// Load the 24 reals of (site, s).
+// Native layout of one right-hand side (of one block): element e = site*Ls + s,
+// 16-byte chunk c of element e at chunk index c * cs + e with cs = nsite*Ls
+// (chunk-major), so the chunk c of consecutive (site, s) is contiguous and a
+// warp's load of one chunk is a contiguous 512-byte segment. FP16/BF16 scales
+// are one float per element at byte offset soff.
 template <class S>
-__device__ __forceinline__ void load24(const char *base, long long soff, int site, int s, int Ls,
+__device__ __forceinline__ void load24(const char *base, long long soff, int cs, int e,
                                        typename S::R *v) {
   if constexpr (std::is_same<S, F32>::value) {
-    const float4 *p = reinterpret_cast<const float4 *>(base) + (size_t)site * 6 * Ls + s;
+    const float4 *p = reinterpret_cast<const float4 *>(base) + e;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      float4 q = __ldg(p + k * Ls);
+      float4 q = __ldg(p + (size_t)k * cs);
       v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
     }
   } else if constexpr (std::is_same<S, F64>::value) {
-    const double2 *p = reinterpret_cast<const double2 *>(base) + (size_t)site * 12 * Ls + s;
+    const double2 *p = reinterpret_cast<const double2 *>(base) + e;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      double2 q = __ldg(p + k * Ls);
+      double2 q = __ldg(p + (size_t)k * cs);
       v[2 * k] = q.x; v[2 * k + 1] = q.y;
     }
   } else {
-    const uint4 *p = reinterpret_cast<const uint4 *>(base) + (size_t)site * 3 * Ls + s;
-    const float scl = __ldg(reinterpret_cast<const float *>(base + soff) + (size_t)site * Ls + s);
+    const uint4 *p = reinterpret_cast<const uint4 *>(base) + e;
+    const float scl = __ldg(reinterpret_cast<const float *>(base + soff) + e);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) unpack8<S>(__ldg(p + k * Ls), v + 8 * k);
+    for (int k = 0; k < 3; ++k) unpack8<S>(__ldg(p + (size_t)k * cs), v + 8 * k);
 #pragma unroll
     for (int k = 0; k < 24; ++k) v[k] *= scl;
   }
 }
 
-// Load one chirality (UPPER: reals 0..11, else 12..23) of (site, s) into v[0..12).
+// Load one chirality (UPPER: reals 0..11, else 12..23) of element e into v[0..12).
 template <class S, bool UPPER>
-__device__ __forceinline__ void load12(const char *base, long long soff, int site, int s, int Ls,
+__device__ __forceinline__ void load12(const char *base, long long soff, int cs, int e,
                                        typename S::R *v) {
   if constexpr (std::is_same<S, F32>::value) {
-    const float4 *p = reinterpret_cast<const float4 *>(base) + (size_t)site * 6 * Ls + s +
-                      (UPPER ? 0 : 3 * Ls);
+    const float4 *p = reinterpret_cast<const float4 *>(base) + e + (UPPER ? 0 : (size_t)3 * cs);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      float4 q = __ldg(p + k * Ls);
+      float4 q = __ldg(p + (size_t)k * cs);
       v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
     }
   } else if constexpr (std::is_same<S, F64>::value) {
-    const double2 *p = reinterpret_cast<const double2 *>(base) + (size_t)site * 12 * Ls + s +
-                       (UPPER ? 0 : 6 * Ls);
+    const double2 *p = reinterpret_cast<const double2 *>(base) + e + (UPPER ? 0 : (size_t)6 * cs);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      double2 q = __ldg(p + k * Ls);
+      double2 q = __ldg(p + (size_t)k * cs);
       v[2 * k] = q.x; v[2 * k + 1] = q.y;
     }
   } else {
-    const uint4 *p = reinterpret_cast<const uint4 *>(base) + (size_t)site * 3 * Ls + s;
-    const float scl = __ldg(reinterpret_cast<const float *>(base + soff) + (size_t)site * Ls + s);
+    const uint4 *p = reinterpret_cast<const uint4 *>(base) + e;
+    const float scl = __ldg(reinterpret_cast<const float *>(base + soff) + e);
     float w[16];
     if (UPPER) {
       unpack8<S>(__ldg(p), w);
-      unpack8<S>(__ldg(p + Ls), w + 8);
+      unpack8<S>(__ldg(p + cs), w + 8);
 #pragma unroll
       for (int k = 0; k < 12; ++k) v[k] = w[k] * scl;
     } else {
-      unpack8<S>(__ldg(p + Ls), w);
-      unpack8<S>(__ldg(p + 2 * Ls), w + 8);
+      unpack8<S>(__ldg(p + cs), w);
+      unpack8<S>(__ldg(p + (size_t)2 * cs), w + 8);
 #pragma unroll
       for (int k = 0; k < 12; ++k) v[k] = w[k + 4] * scl;
     }
   }
 }
 
-// Store the 24 reals of (site, s); FP16/BF16 stores v / max|v| and the scale.
+// Store the 24 reals of element e; FP16/BF16 stores v / max|v| and the scale.
 template <class S>
-__device__ __forceinline__ void store24(char *base, long long soff, int site, int s, int Ls,
+__device__ __forceinline__ void store24(char *base, long long soff, int cs, int e,
                                         const typename S::R *v) {
   if constexpr (std::is_same<S, F32>::value) {
-    float4 *p = reinterpret_cast<float4 *>(base) + (size_t)site * 6 * Ls + s;
+    float4 *p = reinterpret_cast<float4 *>(base) + e;
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      p[k * Ls] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      p[(size_t)k * cs] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
   } else if constexpr (std::is_same<S, F64>::value) {
-    double2 *p = reinterpret_cast<double2 *>(base) + (size_t)site * 12 * Ls + s;
+    double2 *p = reinterpret_cast<double2 *>(base) + e;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) p[k * Ls] = make_double2(v[2 * k], v[2 * k + 1]);
+    for (int k = 0; k < 12; ++k) p[(size_t)k * cs] = make_double2(v[2 * k], v[2 * k + 1]);
   } else {
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(v[k]));
     const float inv = m > 0.f ? 1.0f / m : 0.f;
-    uint4 *p = reinterpret_cast<uint4 *>(base) + (size_t)site * 3 * Ls + s;
+    uint4 *p = reinterpret_cast<uint4 *>(base) + e;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[k * Ls] = pack8<S>(v + 8 * k, inv);
-    reinterpret_cast<float *>(base + soff)[(size_t)site * Ls + s] = m;
+    for (int k = 0; k < 3; ++k) p[(size_t)k * cs] = pack8<S>(v + 8 * k, inv);
+    reinterpret_cast<float *>(base + soff)[e] = m;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Link records: 18 reals of U[a][b] (row-major complex) per (owner, mu).
+// Pairs of adjacent elements (e, e+1), e even: chunk c of both is one 32-byte
+// word, moved with a single 256-bit load or store (sm_100 and later). A warp
+// request of 32 such words is one contiguous kilobyte.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void ldg256(const void *p, uint32_t (&a)[8]) {
+  asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]),
+                 "=r"(a[6]), "=r"(a[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void stg256(void *p, const uint32_t (&a)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(a[0]),
+               "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7])
+               : "memory");
+}
+
+// Load the 24 reals of elements e (v0) and e+1 (v1); e even. FP32/FP16/BF16.
 template <class S>
-__device__ __forceinline__ void load_link(const char *links, int owner, int mu,
-                                          typename S::R *u) {
-  const size_t rec = (size_t)owner * 4 + mu;
+__device__ __forceinline__ void load24x2(const char *base, long long soff, int cs, int e,
+                                         float *v0, float *v1) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(base) + e;
+  if constexpr (std::is_same<S, F32>::value) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      uint32_t a[8];
+      ldg256(p + (size_t)k * cs, a);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v0[4 * k + i] = __uint_as_float(a[i]);
+        v1[4 * k + i] = __uint_as_float(a[4 + i]);
+      }
+    }
+  } else {
+    const float2 scl = __ldg(reinterpret_cast<const float2 *>(base + soff) + e / 2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint32_t a[8];
+      ldg256(p + (size_t)k * cs, a);
+      unpack8<S>(make_uint4(a[0], a[1], a[2], a[3]), v0 + 8 * k);
+      unpack8<S>(make_uint4(a[4], a[5], a[6], a[7]), v1 + 8 * k);
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      v0[k] *= scl.x;
+      v1[k] *= scl.y;
+    }
+  }
+}
+
+// Store the 24 reals of elements e (v0) and e+1 (v1); e even. FP16/BF16 store
+// each element relative to its own maximum.
+template <class S>
+__device__ __forceinline__ void store24x2(char *base, long long soff, int cs, int e,
+                                          const float *v0, const float *v1) {
+  uint4 *p = reinterpret_cast<uint4 *>(base) + e;
+  if constexpr (std::is_same<S, F32>::value) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      uint32_t a[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = __float_as_uint(v0[4 * k + i]);
+        a[4 + i] = __float_as_uint(v1[4 * k + i]);
+      }
+      stg256(p + (size_t)k * cs, a);
+    }
+  } else {
+    float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      m0 = fmaxf(m0, fabsf(v0[k]));
+      m1 = fmaxf(m1, fabsf(v1[k]));
+    }
+    const float i0 = m0 > 0.f ? 1.0f / m0 : 0.f, i1 = m1 > 0.f ? 1.0f / m1 : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint4 q0 = pack8<S>(v0 + 8 * k, i0), q1 = pack8<S>(v1 + 8 * k, i1);
+      const uint32_t a[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      stg256(p + (size_t)k * cs, a);
+    }
+    reinterpret_cast<float2 *>(base + soff)[e / 2] = make_float2(m0, m1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Link records: 18 reals of U[a][b] (row-major complex) per (owner, mu), in
+// kLinkChunks 16-byte words (FP64 9, FP32 5, FP16 3).
+// ---------------------------------------------------------------------------
+// Load the link record whose word 0 is at w; word k is at w[k * ws] (the
+// chunk-major link layout: ws = number of link owners).
+template <class S>
+__device__ __forceinline__ void load_link(const uint4 *w, size_t ws, typename S::R *u) {
   if constexpr (std::is_same<S, F64>::value) {
-    const double2 *p = reinterpret_cast<const double2 *>(links) + rec * 9;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      double2 q = __ldg(p + k);
+      const double2 q = __ldg(reinterpret_cast<const double2 *>(w + k * ws));
       u[2 * k] = q.x; u[2 * k + 1] = q.y;
     }
   } else if constexpr (std::is_same<S, F32>::value) {
-    const float4 *p = reinterpret_cast<const float4 *>(links) + rec * 5;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      float4 q = __ldg(p + k);
+      const float4 q = __ldg(reinterpret_cast<const float4 *>(w + k * ws));
       u[4 * k] = q.x; u[4 * k + 1] = q.y; u[4 * k + 2] = q.z; u[4 * k + 3] = q.w;
     }
-    float2 q = __ldg(reinterpret_cast<const float2 *>(p + 4));
+    const float2 q = __ldg(reinterpret_cast<const float2 *>(w + 4 * ws));
     u[16] = q.x; u[17] = q.y;
   } else {
-    const uint4 *p = reinterpret_cast<const uint4 *>(links) + rec * 3;
-    float w[24];
+    float t[24];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) unpack8<F16>(__ldg(p + k), w + 8 * k);
+    for (int k = 0; k < 3; ++k) unpack8<F16>(__ldg(w + k * ws), t + 8 * k);
 #pragma unroll
-    for (int k = 0; k < 18; ++k) u[k] = w[k];
+    for (int k = 0; k < 18; ++k) u[k] = t[k];
   }
 }
 
@@ -178,30 +263,38 @@ __device__ __forceinline__ void load_link(const char *links, int owner, int mu,
 // y_j = v_j + r y_{j-1} (in the shift's own index order).
 // ---------------------------------------------------------------------------
 template <class R>
+__device__ __forceinline__ const LsK<R> &kc(const LsCoef &c) {
+  if constexpr (std::is_same<R, float>::value)
+    return c.f;
+  else
+    return c.d;
+}
+
+template <class R>
 __device__ __forceinline__ void ls_column(R *T, const R *X, int Ls, bool down, bool inv,
-                                          const LsCoef &c) {
+                                          const LsK<R> &c) {
   auto ix = [&](int j) { return down ? j : Ls - 1 - j; };
-  const R mf = (R)c.mf;
+  const R mf = c.mf;
   if (inv) {
-    const R r = (R)c.r;
+    const R r = c.r;
     R acc = 0, rk = r;
     for (int k = 1; k < Ls; ++k) {
       acc += rk * T[ix(Ls - k)];
       rk *= r;
     }
-    R y = (T[ix(0)] - mf * acc) * (R)c.inv_den;
+    R y = (T[ix(0)] - mf * acc) * c.inv_den;
     T[ix(0)] = y;
     for (int j = 1; j < Ls; ++j) {
       y = T[ix(j)] + r * y;
       T[ix(j)] = y;
     }
   }
-  const R p0 = (R)(c.q0 * c.p0), p1 = (R)(c.q0 * c.p1);
+  const R p0 = c.p0q, p1 = c.p1q;
   const R last = T[ix(Ls - 1)];
   for (int j = Ls - 1; j >= 1; --j) T[ix(j)] = p0 * T[ix(j)] + p1 * T[ix(j - 1)];
   T[ix(0)] = p0 * T[ix(0)] - p1 * mf * last;
   if (X) {
-    const R a0 = (R)c.a0, a1 = (R)c.a1;
+    const R a0 = c.a0, a1 = c.a1;
     for (int j = 1; j < Ls; ++j) T[ix(j)] += a0 * X[ix(j)] + a1 * X[ix(j - 1)];
     T[ix(0)] += a0 * X[ix(0)] - a1 * mf * X[ix(Ls - 1)];
   }

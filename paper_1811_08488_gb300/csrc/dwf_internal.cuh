@@ -94,21 +94,40 @@ struct FieldRef {
   long long bstride = 0;  // bytes between blocks (block-local fields)
   long long rstride = 0;  // bytes between right-hand sides
   long long scale_off = 0;  // byte offset of the scale array from data (half)
+  int cs = 0;               // elements per chunk plane: nsite * Ls
 };
 
 // Ls-direction operator applied in the epilogue of a hop kernel, per rhs:
 //   out = q0 (p0 + p1 S) [(1 - r S)^-1 if inv] acc  +  (a0 + a1 S) xown
 // with S the chiral shift (wrap factor -mf). The direction of S on each
 // chirality is fixed by the kernel's dagger flag.
+// Copies of the coefficients in the kernel's arithmetic type, filled on the
+// host by finalize_coef(): FP32 kernels then do no FP64 arithmetic or
+// conversion (GB300's FP64 pipe is a small fraction of its FP32 pipe).
+template <class R>
+struct LsK {
+  R p0q, p1q;  // q0 * p0, q0 * p1
+  R r, inv_den, a0, a1, mf, pre_b, pre_c, q0;
+};
+
 struct LsCoef {
   double q0, p0, p1, r, inv_den, a0, a1, mf;
   double pre_b, pre_c;  // M_phi applied to the hop input (b + c S)
+  LsK<float> f;
+  LsK<double> d;
 };
+
+inline void finalize_coef(LsCoef &c) {
+  c.d = {c.q0 * c.p0, c.q0 * c.p1, c.r, c.inv_den, c.a0, c.a1, c.mf, c.pre_b, c.pre_c, c.q0};
+  c.f = {(float)c.d.p0q, (float)c.d.p1q, (float)c.r, (float)c.inv_den, (float)c.a0,
+         (float)c.a1, (float)c.mf, (float)c.pre_b, (float)c.pre_c, (float)c.q0};
+}
 
 struct HopParams {
   FieldRef in, out, xown, dotv;
   const char *links = nullptr;
   long long link_bstride = 0;
+  int link_cs = 0;  // link owners per block: word k of (owner, mu) at (mu*words + k)*link_cs + owner
   const int *nbr = nullptr;  // [n_out][8], direction 2*mu + (0 fwd, 1 bwd)
   int n_out = 0;             // output sites per block
   int in_limit = 0;          // inputs with index >= in_limit are zero
@@ -225,7 +244,7 @@ namespace dwf {
 template <class S>
 void launch_hop(const HopParams &P, int dagger, int pre_mphi, int nrhs, cudaStream_t st);
 int hop_sites_per_cta(int Ls, dwf_prec p);
-size_t hop_smem_bytes(int Ls, dwf_prec p, int has_x);
+size_t hop_smem_bytes(int Ls, dwf_prec p, int epi, int has_x);
 
 // ls.cu: Ls-local operators (M_5, M_5^-1) on native fields
 void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride,

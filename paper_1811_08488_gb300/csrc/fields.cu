@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) ls_kernel(char *out, const char *in, long
   char *op = out + rhs * rstride;
   if (active) {
     R v[24];
-    load24<S>(ip, soff, site, s, Ls, v);
+    load24<S>(ip, soff, nsite * Ls, site * Ls + s, v);
 #pragma unroll
     for (int k = 0; k < 24; ++k) T[(sl * 24 + k) * col + s] = v[k];
   }
@@ -34,21 +34,24 @@ __global__ void __launch_bounds__(256) ls_kernel(char *out, const char *in, long
   for (int w = tid; w < nsites * 24; w += blockDim.x) {
     if (blockIdx.x * nsites + w / 24 >= nsite) continue;
     const bool down = ((w % 24) < 12) != DAG;
-    ls_column<R>(T + w * col, nullptr, Ls, down, inv != 0, P.coef[rhs]);
+    ls_column<R>(T + w * col, nullptr, Ls, down, inv != 0, kc<R>(P.coef[rhs]));
   }
   __syncthreads();
   if (active) {
     R v[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) v[k] = T[(sl * 24 + k) * col + s];
-    store24<S>(op, soff, site, s, Ls, v);
+    store24<S>(op, soff, nsite * Ls, site * Ls + s, v);
   }
 }
 
 void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride, int nsite, int Ls,
                   int dagger, int inv, int nrhs, const LsCoef *coef, cudaStream_t st) {
   HopParams P;
-  for (int r = 0; r < nrhs; ++r) P.coef[r] = coef[r];
+  for (int r = 0; r < nrhs; ++r) {
+    P.coef[r] = coef[r];
+    finalize_coef(P.coef[r]);
+  }
   const int nsites = hop_sites_per_cta(Ls, p);
   P.nsites = nsites;
   dim3 grid((nsite + nsites - 1) / nsites, 1, nrhs), block((nsites * Ls + 31) / 32 * 32);
@@ -87,7 +90,7 @@ __global__ void import_kernel(char *native, long long nstride, long long soff, c
     typename S::R v[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) v[k] = (typename S::R)src[k];
-    store24<S>(native + rhs * nstride, soff, h, s, Ls, v);
+    store24<S>(native + rhs * nstride, soff, nsite * Ls, (int)i, v);
   }
 }
 
@@ -101,7 +104,7 @@ __global__ void export_kernel(C *canon, const char *native, long long nstride, l
     const int h = (int)(i / Ls), s = (int)(i % Ls);
     C *dst = canon + (((size_t)rhs * Ls + s) * nsite + h) * 24;
     typename S::R v[24];
-    load24<S>(native + rhs * nstride, soff, h, s, Ls, v);
+    load24<S>(native + rhs * nstride, soff, nsite * Ls, (int)i, v);
 #pragma unroll
     for (int k = 0; k < 24; ++k) dst[k] = (C)v[k];
   }
@@ -154,9 +157,13 @@ void launch_export(dwf_prec p, void *canon, int canon_fp32, const char *native, 
 }
 
 // ---------------------------------------------------------------------------
-// Gauge links. Input U[t][z][y][x][mu][3][3] complex128; output records
-// [owner][mu] with owner = parity * Vh + idx/2 (the combined numbering). The
-// link leaving t = Lt-1 carries the antiperiodic sign.
+// Gauge links. Input U[t][z][y][x][mu][3][3] complex128. Each link record
+// (owner, mu) -- owner = parity * Vh + idx/2, the combined numbering -- is cut
+// into 16-byte words (FP64 9, FP32 5, FP16 3: 18 reals, zero padded), stored
+// chunk-major: word k of (owner, mu) at index (mu * words + k) * nown + owner,
+// nown = V4. Consecutive owners' words are adjacent, so the link loads of the
+// sites of a warp are contiguous. The link leaving t = Lt-1 carries the
+// antiperiodic sign.
 // ---------------------------------------------------------------------------
 __global__ void pack_links_kernel(const double *U, double *l64, float *l32, __half *l16, int Lx,
                                   int Ly, int Lz, int Lt, int tap) {
@@ -166,19 +173,19 @@ __global__ void pack_links_kernel(const double *U, double *l64, float *l32, __ha
     const int x = idx % Lx, y = (idx / Lx) % Ly, z = (idx / (Lx * Ly)) % Lz,
               t = idx / (Lx * Ly * Lz);
     const int par = (x + y + z + t) & 1;
-    const int owner = par * Vh + (idx >> 1);
+    const size_t owner = (size_t)par * Vh + (idx >> 1);
     const double sgn = (tap && mu == 3 && t == Lt - 1) ? -1.0 : 1.0;
     const double *src = U + (size_t)i * 18;
-    const size_t rec = (size_t)owner * 4 + mu;
-    for (int k = 0; k < 18; ++k) {
-      const double v = sgn * src[k];
-      l64[rec * 18 + k] = v;
-      l32[rec * 20 + k] = (float)v;
-      l16[rec * 24 + k] = __double2half(v);
-    }
-    l32[rec * 20 + 18] = 0.f;
-    l32[rec * 20 + 19] = 0.f;
-    for (int k = 18; k < 24; ++k) l16[rec * 24 + k] = __double2half(0.0);
+    double v[24];
+    for (int k = 0; k < 24; ++k) v[k] = k < 18 ? sgn * src[k] : 0.0;
+    for (int w = 0; w < 9; ++w)  // FP64: 2 reals per word
+      for (int q = 0; q < 2; ++q) l64[(((size_t)mu * 9 + w) * V4 + owner) * 2 + q] = v[2 * w + q];
+    for (int w = 0; w < 5; ++w)  // FP32: 4 reals per word
+      for (int q = 0; q < 4; ++q)
+        l32[(((size_t)mu * 5 + w) * V4 + owner) * 4 + q] = (float)v[4 * w + q];
+    for (int w = 0; w < 3; ++w)  // FP16: 8 reals per word
+      for (int q = 0; q < 8; ++q)
+        l16[(((size_t)mu * 3 + w) * V4 + owner) * 8 + q] = __double2half(v[8 * w + q]);
   }
 }
 
@@ -189,28 +196,31 @@ void launch_pack_links(const double *U, char *l64, char *l32, char *l16, const i
   DWF_CUDA_TRY(cudaGetLastError());
 }
 
-// Per-block link copies: dst[block][c][mu] = record of global owner gowner[block][c]
-// (owner ids in the combined numbering parity * Vh + idx/2).
+// Per-block link copies, chunk-major per block: word k of (local owner c, mu)
+// of block b at index b * 4 * words * n_comb + (mu * words + k) * n_comb + c,
+// copied from the global record of owner gowner[b][c].
 __global__ void block_links_kernel(char *dst, const char *src, int words, const int *gowner,
-                                   long long nrec) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrec * words;
+                                   int n_comb, int nblocks, int nown) {
+  const long long per_block = 4LL * words * n_comb;
+  const long long n = per_block * nblocks;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / words;
-    const int w = (int)(i % words);
-    const int owner = gowner[r / 4];
-    const int mu = (int)(r % 4);
-    const uint4 *s = reinterpret_cast<const uint4 *>(src) + ((size_t)owner * 4 + mu) * words + w;
-    reinterpret_cast<uint4 *>(dst)[r * words + w] = __ldg(s);
+    const int b = (int)(i / per_block);
+    const long long r = i - b * per_block;
+    const int mw = (int)(r / n_comb), c = (int)(r % n_comb);
+    const int owner = gowner[(size_t)b * n_comb + c];
+    reinterpret_cast<uint4 *>(dst)[i] =
+        __ldg(reinterpret_cast<const uint4 *>(src) + (size_t)mw * nown + owner);
   }
 }
 
 void launch_block_links(dwf_prec p, char *dst, const char *src_l32, const char *src_l16,
-                        const int *gowner, int n_comb, int nblocks, const int *,
+                        const int *gowner, int n_comb, int nblocks, const int *dims,
                         cudaStream_t st) {
   const int rec = (int)link_record_bytes(p == DWF_FP32 ? DWF_FP32 : DWF_FP16);
   const char *src = (p == DWF_FP32) ? src_l32 : src_l16;
-  block_links_kernel<<<1024, 256, 0, st>>>(dst, src, rec / 16, gowner,
-                                           (long long)nblocks * n_comb * 4);
+  const int V4 = dims[0] * dims[1] * dims[2] * dims[3];
+  block_links_kernel<<<1024, 256, 0, st>>>(dst, src, rec / 16, gowner, n_comb, nblocks, V4);
   DWF_CUDA_TRY(cudaGetLastError());
 }
 

@@ -63,28 +63,42 @@ __device__ __forceinline__ void adag_times(const Cx<R> w0, const Cx<R> w1, Cx<R>
   }
 }
 
+template <class R, int MU, bool FWD, bool DAG>
+__device__ __forceinline__ void proj_mul_acc(R *acc, const R *v, const R *u);
+
 // One direction of the hop: project, multiply by U or U^+, reconstruct, add.
+// `lk` is the link record.
 template <class S, int MU, bool FWD, bool DAG, bool PRE>
 __device__ __forceinline__ void hop_dir(typename S::R *acc, const char *in, long long soff,
-                                        int j, int s, int Ls, const char *links, int owner,
-                                        const LsCoef &cf) {
+                                        int cs, int j, int s, int Ls, const uint4 *lk,
+                                        size_t ls, const LsCoef &cf) {
   using R = typename S::R;
   R v[24];
-  load24<S>(in, soff, j, s, Ls, v);
+  load24<S>(in, soff, cs, j * Ls + s, v);
   if constexpr (PRE) {
     R w[12];
-    const R b = (R)cf.pre_b, c = (R)cf.pre_c, mf = (R)cf.mf;
+    const LsK<R> &kk = kc<R>(cf);
+    const R b = kk.pre_b, c = kk.pre_c, mf = kk.mf;
     const int sm = s == 0 ? Ls - 1 : s - 1;
     const R fm = s == 0 ? -mf : (R)1;
-    load12<S, true>(in, soff, j, sm, Ls, w);
+    load12<S, true>(in, soff, cs, j * Ls + sm, w);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = b * v[k] + c * fm * w[k];
     const int sp = s == Ls - 1 ? 0 : s + 1;
     const R fp = s == Ls - 1 ? -mf : (R)1;
-    load12<S, false>(in, soff, j, sp, Ls, w);
+    load12<S, false>(in, soff, cs, j * Ls + sp, w);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[12 + k] = b * v[12 + k] + c * fp * w[k];
   }
+  R u[18];
+  load_link<S>(lk, ls, u);
+  proj_mul_acc<R, MU, FWD, DAG>(acc, v, u);
+}
+
+// Project v with (1 - sg g_mu), multiply the two-spinor by U (forward) or U^+
+// (backward), reconstruct and add to acc.
+template <class R, int MU, bool FWD, bool DAG>
+__device__ __forceinline__ void proj_mul_acc(R *acc, const R *v, const R *u) {
   constexpr R sg = (FWD != DAG) ? (R)1 : (R)-1;  // projector (1 - sg g_mu)
   Cx<R> h[2][3];
 #pragma unroll
@@ -98,8 +112,6 @@ __device__ __forceinline__ void hop_dir(typename S::R *acc, const char *in, long
     h[0][c] = {v0.re - sg * a0.re, v0.im - sg * a0.im};
     h[1][c] = {v1.re - sg * a1.re, v1.im - sg * a1.im};
   }
-  R u[18];
-  load_link<S>(links, owner, MU, u);
   Cx<R> w[2][3];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
@@ -134,17 +146,47 @@ __device__ __forceinline__ void hop_dir(typename S::R *acc, const char *in, long
 
 template <class S, int MU, bool DAG, bool PRE>
 __device__ __forceinline__ void hop_mu(typename S::R *acc, const HopParams &P, const char *in,
-                                       const char *links, const int *nb, int site, int s,
+                                       const uint4 *links, const int *nb, int site, int s,
                                        const LsCoef &cf) {
+  constexpr int LC = S::kLinkChunks;
   const int jf = nb[2 * MU], jb = nb[2 * MU + 1];
+  const size_t ls = (size_t)P.link_cs;
+  const uint4 *lmu = links + (size_t)MU * LC * ls;
   if (jf >= 0 && jf < P.in_limit)
-    hop_dir<S, MU, true, DAG, PRE>(acc, in, P.in.scale_off, jf, s, P.Ls, links,
-                                   P.out_link_off + site, cf);
+    hop_dir<S, MU, true, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jf, s, P.Ls,
+                                   lmu + P.out_link_off + site, ls, cf);
   if (jb >= 0 && jb < P.in_limit)
-    hop_dir<S, MU, false, DAG, PRE>(acc, in, P.in.scale_off, jb, s, P.Ls, links,
-                                    P.in_link_off + jb, cf);
+    hop_dir<S, MU, false, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jb, s, P.Ls,
+                                    lmu + P.in_link_off + jb, ls, cf);
 }
 
+// Shared memory of one CTA for the Ls epilogue: the hop result T and the
+// own-site input X as [site][component][Ls + 1] columns.
+template <class R>
+__device__ __forceinline__ void epilogue_columns(R *T, const R *X, int nsites, int site0,
+                                                 int n_out, int Ls, bool dag, int inv,
+                                                 const LsCoef &cf) {
+  const int col = Ls + 1;
+  for (int w = threadIdx.x; w < nsites * 24; w += blockDim.x) {
+    if (site0 + w / 24 >= n_out) continue;
+    const bool down = ((w % 24) < 12) != dag;
+    ls_column<R>(T + w * col, X ? X + w * col : nullptr, Ls, down, inv != 0, kc<R>(cf));
+  }
+}
+
+// Publish the CTA's part of Re<dotv, out> (both summed per (rhs, block)).
+__device__ __forceinline__ void hop_dot(const HopParams &P, double d, double *red, int rhs,
+                                        int blk) {
+  d = cta_sum(d, red);
+  const int ntiles = gridDim.x;
+  const int grp = rhs * P.nblocks + blk;
+  double total;
+  if (group_reduce(d, P.partials + (size_t)grp * ntiles, ntiles, blockIdx.x, P.counters + grp,
+                   total))
+    P.dot_out[(size_t)rhs * P.dot_rstride + blk] = total;
+}
+
+// One thread per output (site, s): used for FP64 fields and odd Ls.
 template <class S, bool DAG, bool PRE>
 __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopParams P) {
   using R = typename S::R;
@@ -156,13 +198,14 @@ __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopPar
   const int nsites = P.nsites;  // blockDim.x is nsites * Ls rounded up to whole warps
   const int tid = threadIdx.x;
   const int s = tid % Ls, sl = tid / Ls;
-  const int site = blockIdx.x * nsites + sl;
+  const int site0 = blockIdx.x * nsites;
+  const int site = site0 + sl;
   const bool active = (sl < nsites) && (site < P.n_out);
   const LsCoef &cf = P.coef[rhs];
 
   const char *in = P.in.data + blk * P.in.bstride + rhs * P.in.rstride;
   char *out = P.out.data + blk * P.out.bstride + rhs * P.out.rstride;
-  const char *links = P.links + blk * P.link_bstride;
+  const uint4 *links = reinterpret_cast<const uint4 *>(P.links + blk * P.link_bstride);
 
   R acc[24];
 #pragma unroll
@@ -174,6 +217,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopPar
     hop_mu<S, 2, DAG, PRE>(acc, P, in, links, nb, site, s, cf);
     hop_mu<S, 3, DAG, PRE>(acc, P, in, links, nb, site, s, cf);
   }
+  const int e = site * Ls + s;
 
   if (P.epi) {
     const int col = Ls + 1;
@@ -186,7 +230,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopPar
         R xv[24];
         if (site < P.xown_limit) {
           const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
-          load24<S>(xo, P.xown.scale_off, site, s, Ls, xv);
+          load24<S>(xo, P.xown.scale_off, P.xown.cs, e, xv);
         } else {
 #pragma unroll
           for (int k = 0; k < 24; ++k) xv[k] = 0;
@@ -196,64 +240,314 @@ __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopPar
       }
     }
     __syncthreads();
-    for (int w = tid; w < nsites * 24; w += blockDim.x) {
-      const int wsite = blockIdx.x * nsites + w / 24;
-      if (wsite >= P.n_out) continue;
-      const int comp = w % 24;
-      const bool down = (comp < 12) != DAG;
-      ls_column<R>(T + w * col, P.has_x ? X + w * col : nullptr, Ls, down, P.inv != 0, cf);
-    }
+    epilogue_columns<R>(T, P.has_x ? X : nullptr, nsites, site0, P.n_out, Ls, DAG, P.inv, cf);
     __syncthreads();
     if (active) {
 #pragma unroll
       for (int k = 0; k < 24; ++k) acc[k] = T[(sl * 24 + k) * col + s];
     }
   } else {
-    const R q = (R)cf.q0;
+    const R q = kc<R>(cf).q0;
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] *= q;
   }
-  if (active) store24<S>(out, P.out.scale_off, site, s, Ls, acc);
+  if (active) store24<S>(out, P.out.scale_off, P.out.cs, e, acc);
 
   if (P.dot) {
     double d = 0.0;
     if (active) {
       R dv[24];
       const char *dp = P.dotv.data + blk * P.dotv.bstride + rhs * P.dotv.rstride;
-      load24<S>(dp, P.dotv.scale_off, site, s, Ls, dv);
+      load24<S>(dp, P.dotv.scale_off, P.dotv.cs, e, dv);
+      R part = 0;
 #pragma unroll
-      for (int k = 0; k < 24; ++k) d += (double)dv[k] * (double)acc[k];
+      for (int k = 0; k < 24; ++k) part += dv[k] * acc[k];
+      d = (double)part;
     }
-    d = cta_sum(d, red);
-    const int ntiles = gridDim.x;
-    const int grp = rhs * P.nblocks + blk;
-    double total;
-    if (group_reduce(d, P.partials + (size_t)grp * ntiles, ntiles, blockIdx.x, P.counters + grp,
-                     total))
-      P.dot_out[(size_t)rhs * P.dot_rstride + blk] = total;
+    hop_dot(P, d, red, rhs, blk);
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two slices per thread: thread (site, s0 = 2j) computes s0 and s0 + 1. Chunk c
+// of both slices is one 32-byte word, so every spinor load and store is a
+// 256-bit access and a warp moves one contiguous kilobyte per instruction; the
+// link is loaded once for both slices; with M_phi on load, the two slices
+// supply each other's s -> s +- 1 neighbours and only the outer two halves
+// (s0 - 1 upper, s0 + 2 lower) are loaded in addition. Arithmetic runs on
+// float2 pairs (slice s0, slice s0 + 1) with Blackwell's packed FP32
+// instructions, so each multiply-add serves both slices. FP32/FP16/BF16, even Ls.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+// x + sgn * y on both lanes (sgn = +-1 at compile time): one packed FMA.
+template <int SGN>
+__device__ __forceinline__ float2 pm(float2 x, float2 y) {
+  return __ffma2_rn(y, make_float2((float)SGN, (float)SGN), x);
+}
+struct C2 {
+  float2 re, im;
+};
+// x + sgn * (ph * z), ph = i^PH (PH = 0: 1, 1: i, 2: -1, 3: -i).
+template <int PH, int SGN>
+__device__ __forceinline__ C2 add_phase(C2 x, C2 z) {
+  if constexpr (PH == 0) return {pm<SGN>(x.re, z.re), pm<SGN>(x.im, z.im)};
+  else if constexpr (PH == 1) return {pm<-SGN>(x.re, z.im), pm<SGN>(x.im, z.re)};
+  else if constexpr (PH == 2) return {pm<-SGN>(x.re, z.re), pm<-SGN>(x.im, z.im)};
+  else return {pm<SGN>(x.re, z.im), pm<-SGN>(x.im, z.re)};
+}
+// (A v_l)_sp = i^PH v_l[SRC]: per direction mu, for output spin 0 and 1.
+template <int MU> struct ProjA;
+template <> struct ProjA<0> { static constexpr int s0 = 1, p0 = 3, s1 = 0, p1 = 3; };  // -i s1
+template <> struct ProjA<1> { static constexpr int s0 = 1, p0 = 2, s1 = 0, p1 = 0; };  // -i s2
+template <> struct ProjA<2> { static constexpr int s0 = 0, p0 = 3, s1 = 1, p1 = 1; };  // -i s3
+template <> struct ProjA<3> { static constexpr int s0 = 0, p0 = 0, s1 = 1, p1 = 0; };  // 1
+// (A^+ w)_sp = i^PH w[SRC].
+template <int MU> struct ProjAd;
+template <> struct ProjAd<0> { static constexpr int s0 = 1, p0 = 1, s1 = 0, p1 = 1; };
+template <> struct ProjAd<1> { static constexpr int s0 = 1, p0 = 0, s1 = 0, p1 = 2; };
+template <> struct ProjAd<2> { static constexpr int s0 = 0, p0 = 1, s1 = 1, p1 = 3; };
+template <> struct ProjAd<3> { static constexpr int s0 = 0, p0 = 0, s1 = 1, p1 = 0; };
+
+// Packed counterpart of proj_mul_acc: v, acc hold 24 reals of both slices.
+template <int MU, bool FWD, bool DAG>
+__device__ __forceinline__ void proj_mul_acc2(float2 *acc, const float2 *v, const float *u) {
+  constexpr int SG = (FWD != DAG) ? 1 : -1;  // projector (1 - SG g_mu)
+  using A = ProjA<MU>;
+  using Ad = ProjAd<MU>;
+  C2 h[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const C2 vu0{v[0 * 6 + 2 * c], v[0 * 6 + 2 * c + 1]};
+    const C2 vu1{v[1 * 6 + 2 * c], v[1 * 6 + 2 * c + 1]};
+    const C2 vl[2] = {{v[2 * 6 + 2 * c], v[2 * 6 + 2 * c + 1]},
+                      {v[3 * 6 + 2 * c], v[3 * 6 + 2 * c + 1]}};
+    h[0][c] = add_phase<A::p0, -SG>(vu0, vl[A::s0]);
+    h[1][c] = add_phase<A::p1, -SG>(vu1, vl[A::s1]);
+  }
+  C2 w[2][3];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        // forward: U[a][b]; backward: conj(U[b][a])
+        const float ur = FWD ? u[2 * (3 * a + b)] : u[2 * (3 * b + a)];
+        const float ui = FWD ? u[2 * (3 * a + b) + 1] : -u[2 * (3 * b + a) + 1];
+        re = __ffma2_rn(bc(ur), h[sp][b].re, re);
+        re = __ffma2_rn(bc(-ui), h[sp][b].im, re);
+        im = __ffma2_rn(bc(ur), h[sp][b].im, im);
+        im = __ffma2_rn(bc(ui), h[sp][b].re, im);
+      }
+      w[sp][a] = {re, im};
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[0 * 6 + 2 * c] = __fadd2_rn(acc[0 * 6 + 2 * c], w[0][c].re);
+    acc[0 * 6 + 2 * c + 1] = __fadd2_rn(acc[0 * 6 + 2 * c + 1], w[0][c].im);
+    acc[1 * 6 + 2 * c] = __fadd2_rn(acc[1 * 6 + 2 * c], w[1][c].re);
+    acc[1 * 6 + 2 * c + 1] = __fadd2_rn(acc[1 * 6 + 2 * c + 1], w[1][c].im);
+    const C2 l0{acc[2 * 6 + 2 * c], acc[2 * 6 + 2 * c + 1]};
+    const C2 l1{acc[3 * 6 + 2 * c], acc[3 * 6 + 2 * c + 1]};
+    const C2 n0 = add_phase<Ad::p0, -SG>(l0, w[Ad::s0][c]);
+    const C2 n1 = add_phase<Ad::p1, -SG>(l1, w[Ad::s1][c]);
+    acc[2 * 6 + 2 * c] = n0.re;
+    acc[2 * 6 + 2 * c + 1] = n0.im;
+    acc[3 * 6 + 2 * c] = n1.re;
+    acc[3 * 6 + 2 * c + 1] = n1.im;
+  }
+}
+
+template <class S, int MU, bool FWD, bool DAG, bool PRE>
+__device__ __forceinline__ void hop_dir2(float2 *acc, const char *in, long long soff, int cs,
+                                         int j, int s0, int Ls, const uint4 *lk, size_t ls,
+                                         const LsCoef &cf) {
+  float v0[24], v1[24];
+  load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
+  if constexpr (PRE) {
+    const float b = cf.f.pre_b, c = cf.f.pre_c, mf = cf.f.mf;
+    float w[12];
+    const int sm = s0 == 0 ? Ls - 1 : s0 - 1;
+    const float fm = s0 == 0 ? -mf : 1.f;
+    load12<S, true>(in, soff, cs, j * Ls + sm, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {  // upper: chi(s0) <- s0-1, chi(s0+1) <- s0
+      const float t = v0[k];
+      v0[k] = b * t + c * fm * w[k];
+      v1[k] = b * v1[k] + c * t;
+    }
+    const int sp = s0 + 2 == Ls ? 0 : s0 + 2;
+    const float fp = s0 + 2 == Ls ? -mf : 1.f;
+    load12<S, false>(in, soff, cs, j * Ls + sp, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {  // lower: chi(s0) <- s0+1, chi(s0+1) <- s0+2
+      const float t = v1[12 + k];
+      v0[12 + k] = b * v0[12 + k] + c * t;
+      v1[12 + k] = b * t + c * fp * w[k];
+    }
+  }
+  float2 v[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) v[k] = make_float2(v0[k], v1[k]);
+  float u[18];
+  load_link<S>(lk, ls, u);
+  proj_mul_acc2<MU, FWD, DAG>(acc, v, u);
+}
+
+template <class S, int MU, bool DAG, bool PRE>
+__device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const char *in,
+                                        const uint4 *links, const int *nb, int site, int s0,
+                                        const LsCoef &cf) {
+  constexpr int LC = S::kLinkChunks;
+  const int jf = nb[2 * MU], jb = nb[2 * MU + 1];
+  const size_t ls = (size_t)P.link_cs;
+  const uint4 *lmu = links + (size_t)MU * LC * ls;
+  if (jf >= 0 && jf < P.in_limit)
+    hop_dir2<S, MU, true, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jf, s0, P.Ls,
+                                    lmu + P.out_link_off + site, ls, cf);
+  if (jb >= 0 && jb < P.in_limit)
+    hop_dir2<S, MU, false, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jb, s0, P.Ls,
+                                     lmu + P.in_link_off + jb, ls, cf);
+}
+
+template <class S, bool DAG, bool PRE>
+__global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ HopParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int rhs = blockIdx.z, blk = blockIdx.y;
+  if (P.skip && P.skip[rhs]) return;
+  const int Ls = P.Ls, np = Ls >> 1;
+  const int nsites = P.nsites;  // blockDim.x is nsites * Ls / 2 rounded up to whole warps
+  const int tid = threadIdx.x;
+  const int jp = tid % np, sl = tid / np;
+  const int s0 = 2 * jp;
+  const int site0 = blockIdx.x * nsites;
+  const int site = site0 + sl;
+  const bool active = (sl < nsites) && (site < P.n_out);
+  const LsCoef &cf = P.coef[rhs];
+
+  const char *in = P.in.data + blk * P.in.bstride + rhs * P.in.rstride;
+  char *out = P.out.data + blk * P.out.bstride + rhs * P.out.rstride;
+  const uint4 *links = reinterpret_cast<const uint4 *>(P.links + blk * P.link_bstride);
+
+  float2 acc[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] = make_float2(0.f, 0.f);
+  if (active) {
+    const int *nb = P.nbr + (size_t)site * 8;
+    hop_mu2<S, 0, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 1, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 2, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 3, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
+  }
+  const int e = site * Ls + s0;
+  float a0[24], a1[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    a0[k] = acc[k].x;
+    a1[k] = acc[k].y;
+  }
+
+  if (P.epi) {
+    const int col = Ls + 1;
+    float *T = reinterpret_cast<float *>(smem_raw);
+    float *X = T + nsites * 24 * col;
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 24; ++k) {
+        T[(sl * 24 + k) * col + s0] = a0[k];
+        T[(sl * 24 + k) * col + s0 + 1] = a1[k];
+      }
+      if (P.has_x) {
+        float x0[24], x1[24];
+        if (site < P.xown_limit) {
+          const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
+          load24x2<S>(xo, P.xown.scale_off, P.xown.cs, e, x0, x1);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 24; ++k) x0[k] = x1[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+          X[(sl * 24 + k) * col + s0] = x0[k];
+          X[(sl * 24 + k) * col + s0 + 1] = x1[k];
+        }
+      }
+    }
+    __syncthreads();
+    epilogue_columns<float>(T, P.has_x ? X : nullptr, nsites, site0, P.n_out, Ls, DAG, P.inv,
+                            cf);
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 24; ++k) {
+        a0[k] = T[(sl * 24 + k) * col + s0];
+        a1[k] = T[(sl * 24 + k) * col + s0 + 1];
+      }
+    }
+  } else {
+    const float q = cf.f.q0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      a0[k] *= q;
+      a1[k] *= q;
+    }
+  }
+  if (active) store24x2<S>(out, P.out.scale_off, P.out.cs, e, a0, a1);
+
+  if (P.dot) {
+    double d = 0.0;
+    if (active) {
+      float d0[24], d1[24];
+      const char *dp = P.dotv.data + blk * P.dotv.bstride + rhs * P.dotv.rstride;
+      load24x2<S>(dp, P.dotv.scale_off, P.dotv.cs, e, d0, d1);
+      float part = 0.f;
+#pragma unroll
+      for (int k = 0; k < 24; ++k) part += d0[k] * a0[k] + d1[k] * a1[k];
+      d = (double)part;
+    }
+    hop_dot(P, d, red, rhs, blk);
+  }
+}
+
+// Two slices per thread for FP32/FP16/BF16 with even Ls; one otherwise.
+static bool hop_pairs(int Ls, dwf_prec p) { return p != DWF_FP64 && Ls % 2 == 0; }
+
 int hop_sites_per_cta(int Ls, dwf_prec p) {
-  int target = (p == DWF_FP64) ? 128 : 256;
-  int n = target / Ls;
+  int n;
+  if (hop_pairs(Ls, p))
+    n = 128 / (Ls / 2);
+  else
+    n = ((p == DWF_FP64) ? 128 : 256) / Ls;
   return n < 1 ? 1 : n;
 }
 
-size_t hop_smem_bytes(int Ls, dwf_prec p, int has_x) {
-  size_t rs = (p == DWF_FP64) ? 8 : 4;
+size_t hop_smem_bytes(int Ls, dwf_prec p, int epi, int has_x) {
+  if (!epi) return 0;
+  const size_t rs = (p == DWF_FP64) ? 8 : 4;
   return (size_t)hop_sites_per_cta(Ls, p) * 24 * (Ls + 1) * rs * (has_x ? 2 : 1);
 }
 
 template <class S, bool DAG, bool PRE>
 static void launch_t(const HopParams &P0, int nrhs, cudaStream_t st, dwf_prec prec) {
   HopParams P = P0;
+  for (int r = 0; r < nrhs; ++r) finalize_coef(P.coef[r]);
   const int nsites = hop_sites_per_cta(P.Ls, prec);
   P.nsites = nsites;
   dim3 grid((P.n_out + nsites - 1) / nsites, P.nblocks, nrhs);
-  dim3 block((nsites * P.Ls + 31) / 32 * 32);
-  size_t smem = P.epi ? hop_smem_bytes(P.Ls, prec, P.has_x) : 0;
+  const size_t smem = hop_smem_bytes(P.Ls, prec, P.epi, P.has_x);
   if (grid.x == 0) return;
+  if constexpr (!std::is_same<S, F64>::value) {
+    if (hop_pairs(P.Ls, prec)) {
+      dim3 block((nsites * (P.Ls / 2) + 31) / 32 * 32);
+      hop2_kernel<S, DAG, PRE><<<grid, block, smem, st>>>(P);
+      DWF_CUDA_TRY(cudaGetLastError());
+      return;
+    }
+  }
+  dim3 block((nsites * P.Ls + 31) / 32 * 32);
   hop_kernel<S, DAG, PRE><<<grid, block, smem, st>>>(P);
   DWF_CUDA_TRY(cudaGetLastError());
 }
@@ -278,15 +572,21 @@ void launch_hop(const HopParams &P, int dagger, int pre_mphi, int nrhs, cudaStre
 
 // Allow the hop kernels more than 48 KB of dynamic shared memory. Called once
 // per device before any launch (and so before any stream capture).
+template <class K>
+static void allow_big_smem(K *kernel) {
+  DWF_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+}
 template <class S>
 static void prepare_one() {
-  const int big = 200 * 1024;
-  DWF_CUDA_TRY(cudaFuncSetAttribute(hop_kernel<S, false, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DWF_CUDA_TRY(cudaFuncSetAttribute(hop_kernel<S, false, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DWF_CUDA_TRY(cudaFuncSetAttribute(hop_kernel<S, true, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  allow_big_smem(hop_kernel<S, false, false>);
+  allow_big_smem(hop_kernel<S, false, true>);
+  allow_big_smem(hop_kernel<S, true, false>);
+  if constexpr (!std::is_same<S, F64>::value) {
+    allow_big_smem(hop2_kernel<S, false, false>);
+    allow_big_smem(hop2_kernel<S, false, true>);
+    allow_big_smem(hop2_kernel<S, true, false>);
+  }
 }
 void prepare_kernels() {
   prepare_one<F64>();

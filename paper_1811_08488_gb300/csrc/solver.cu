@@ -18,6 +18,7 @@ FieldRef global_ref(const dwf_ctx *ctx, dwf_prec p, const void *ptr) {
   f.data = const_cast<char *>(static_cast<const char *>(ptr));
   f.rstride = (long long)field_rhs_bytes(p, ctx->geo.Vh, ctx->act.Ls);
   f.scale_off = (long long)align_up(field_data_bytes(p, ctx->geo.Vh, ctx->act.Ls), 256);
+  f.cs = ctx->geo.Vh * ctx->act.Ls;
   return f;
 }
 
@@ -58,6 +59,7 @@ static HopParams global_params(const dwf_ctx *ctx, dwf_prec p, int out_parity, c
   P.in = global_ref(ctx, p, in);
   P.out = global_ref(ctx, p, out);
   P.links = link_ptr(ctx, p);
+  P.link_cs = ctx->geo.V4;
   P.nbr = ctx->nbr_dev[out_parity].as<int>();
   P.n_out = ctx->geo.Vh;
   P.in_limit = ctx->geo.Vh;
@@ -161,6 +163,7 @@ static FieldRef block_ref(const DevBuf &buf, dwf_prec p, int nsite, int Ls, int 
   f.scale_off = (p == DWF_FP16 || p == DWF_BF16)
                     ? (long long)align_up(field_data_bytes(p, nsite, Ls), 256)
                     : 0;
+  f.cs = nsite * Ls;
   return f;
 }
 
@@ -244,6 +247,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   HopParams base;
   base.links = bp->links.c();
   base.link_bstride = bp->link_bstride;
+  base.link_cs = g.n_comb;
   base.Ls = bp->Ls;
   base.nblocks = g.nblocks;
   base.skip = skip;
@@ -340,6 +344,7 @@ BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double
   B.rglob = r;
   B.zglob = z;
   B.grs = (long long)field_rhs_bytes(DWF_FP32, ctx->geo.Vh, ctx->act.Ls);
+  B.gcs = ctx->geo.Vh * ctx->act.Ls;
   B.gmap = bp->gmap_b.as<int>();
   B.n_b = g.n_b;
   B.Ls = bp->Ls;
@@ -505,7 +510,7 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   A.rs64 = (long long)field_rhs_bytes(DWF_FP64, Vh, Ls);
   A.rslo = (long long)field_rhs_bytes(lo, Vh, Ls);
   A.n4 = (long long)Vh * Ls * 6;
-  A.Ls = Ls;
+  A.cs = (long long)Vh * Ls;
   A.scal = sp->scal.as<OuterScalars>();
   A.partials = sp->partials.as<double>();
   A.counters = sp->counters.as<unsigned int>();
