@@ -128,13 +128,37 @@ def cpu_sample(outer_iters, k, nblocks):
                        f"scaled to {outer_iters} outer iterations x (A + {k} x {nblocks} A_s)")}
 
 
-def cpu_threads():
+def cpu_sample_1core(outer_iters, k, nblocks):
+    """cpu_sample() with every numpy/BLAS thread pool limited to one thread
+    (the oracle's arrays ops are single-threaded numpy): returns (sample, cores)."""
     try:
         import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] or [1])
-    except Exception:
-        return 1
+        with threadpoolctl.threadpool_limits(1):
+            return cpu_sample(outer_iters, k, nblocks), 1
+    except ImportError:
+        return cpu_sample(outer_iters, k, nblocks), 1
+
+
+# Outer iterations of the GB300 MSPCG solve of this workload (measured by the
+# GB300 arm: 118 at k = 6, 8^3 x 16 blocks). The reference arm scales its
+# per-iteration sample by it, since a full FP64 oracle solve takes hours.
+MSPCG_OUTER_ITERS = 118
+
+
+# ----------------------------------------------------------------------------
+# Replicas (N > 1): the step time is the maximum over ranks
+# ----------------------------------------------------------------------------
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of a list of floats over all ranks."""
+    import torch
+    v = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return v.tolist()
+
+
+def replica_source_seed(workload_id, rank):
+    """Each replica solves its own Gaussian source."""
+    return 2000 + workload_id + rank
 
 
 # ----------------------------------------------------------------------------
@@ -154,7 +178,7 @@ def run_gpu(args, rank, world, dist):
     w = syn.WORKLOADS[WORKLOAD]
     dims, Ls, mf = w["dims"], w["Ls"], w["mf"][0]
     Uc = syn.gauge_field(dims, w["eps"], 1000 + w["id"])
-    src = syn.half_field(dims, Ls, 2000 + w["id"] + rank)
+    src = syn.half_field(dims, Ls, replica_source_seed(w["id"], rank))
     ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"], device=dev)
     ctx.gauge_load(Uc)
     stream = torch.cuda.current_stream()
@@ -247,10 +271,7 @@ def run_gpu(args, rank, world, dist):
     t_plain = statistics.mean(t for t, _, _ in plain)
     t_e2e = statistics.mean(e2e_t)
     if dist:
-        import torch.distributed as td
-        v = torch.tensor([t_ms, t_plain, t_e2e], dtype=torch.float64, device="cuda")
-        td.all_reduce(v, op=td.ReduceOp.MAX)
-        t_ms, t_plain, t_e2e = v.tolist()
+        t_ms, t_plain, t_e2e = max_over_ranks([t_ms, t_plain, t_e2e], dist, "cuda")
     info_ms, info_plain = ms[-1][2], plain[-1][2]
     ok = all(st == 0 and i["converged"] for _, st, i in ms + plain)
     k = 6
@@ -319,15 +340,13 @@ def main():
         w = syn.WORKLOADS[WORKLOAD]
         # iteration count of the GB300 MSPCG solve of this workload (measured),
         # used to scale the per-iteration sample
-        outer = int(os.environ.get("MSPCG_OUTER_ITERS", "300"))
         nblocks = 16
         vals = []
         for i in range(args.warmup + args.steps):
-            s = cpu_sample(outer, 6, nblocks)
+            s, cores = cpu_sample_1core(MSPCG_OUTER_ITERS, 6, nblocks)
             if i >= args.warmup:
                 vals.append(s["value"])
         v = statistics.mean(vals)
-        cores = cpu_threads()
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                           "higher_is_better": False, "data": "synthetic", "dtype": "f64",
@@ -348,9 +367,9 @@ def main():
     res, info_ms, nblocks = run_gpu(args, rank, world, dist)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and not args.dslash_only:
-            s = cpu_sample(info_ms["outer_iters"], 6, nblocks)
+            s, cores = cpu_sample_1core(info_ms["outer_iters"], 6, nblocks)
             res["cpu_baseline"] = {"value": round(s["value"], 3), "unit": "s",
-                                   "cores": cpu_threads(), "kind": "oracle", "sample": s["sample"]}
+                                   "cores": cores, "kind": "oracle", "sample": s["sample"]}
         print(json.dumps(res))
     if dist:
         dist.barrier()
