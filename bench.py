@@ -34,6 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MSPCG vs plain CG time-to-solve at resid 1e-10 (1 GB300); Dslash HBM GB/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of hop2_kernel<F32,0,1> on this
+# workload, one ncu capture (124.58 MB + 47.61 MB); see profiles/.
+HOP_FP32_DRAM_BYTES = 172192768
 WORKLOAD = "mobius_16^3x32x12"
 
 
@@ -205,6 +208,26 @@ def run_gpu(args, rank, world, dist):
         times.append(e0.elapsed_time(e1) * 1e-3)
     t_hop = statistics.median(times)
     hop_gbs = alg_bytes / t_hop / 1e9
+
+    # the same kernel on FP16 fields (the storage of the inner block solves,
+    # which take most of the MSPCG time): 48 B + 4 B scale per (site, s),
+    # 36 B FP16 links
+    f16in = ctx.new_field("fp16")
+    f16out = ctx.new_field("fp16")
+    ctx.field_import(f16in, "fp16", canon)
+    alg16 = 2 * Vh * Ls * (48 + 4) + V4 * 4 * 18 * 2
+    for _ in range(5):
+        ctx.dslash_eo(f16out, f16in, 0, 1, "fp16", [mf])
+    times16 = []
+    for _ in range(30):
+        flush_l2(l2_flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.dslash_eo(f16out, f16in, 0, 1, "fp16", [mf])
+        e1.record(stream)
+        e1.synchronize()
+        times16.append(e0.elapsed_time(e1) * 1e-3)
+    t_hop16 = statistics.median(times16)
     if args.dslash_only:
         times_dag = []
         for _ in range(30):
@@ -306,12 +329,18 @@ def run_gpu(args, rank, world, dist):
                      "true_resid": info_plain["true_resid"]},
         "mspcg_speedup_vs_plain": round(t_plain / t_ms, 4),
         "all_converged": ok,
-        "dslash": {"kernel": "hop_kernel<F32,DAG=0,PRE=1> (M^4 = -1/2 Dhop M_phi)",
+        "dslash": {"kernel": "hop2_kernel<F32,DAG=0,PRE=1> (M^4 = -1/2 Dhop M_phi)",
                    "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
                    "gbs": round(hop_gbs, 1), "frac_of_8tbs_nominal": round(hop_gbs / 8000, 4)},
+        "dslash_fp16_dagger": {"kernel": "hop2_kernel<F16,DAG=1,PRE=0>", "us": round(t_hop16 * 1e6, 2),
+                               "alg_bytes": alg16, "gbs": round(alg16 / t_hop16 / 1e9, 1),
+                               "frac": round(alg16 / t_hop16 / 1e9 / peak, 4)},
+        # traffic: dram read + write of this kernel from one ncu capture of
+        # `bench.py --dslash-only` (profiles/hop_fp32_mobius_16x16x16x32_Ls12.md)
         "roofline": {"bound": "hbm", "achieved": round(hop_gbs, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(hop_gbs / peak, 4), "traffic": None,
-                     "kernel": "hop_kernel<F32,0,1>", "peak_kind": kind},
+                     "frac": round(hop_gbs / peak, 4), "traffic": HOP_FP32_DRAM_BYTES,
+                     "kernel": "hop2_kernel<F32,0,1>", "peak_kind": kind,
+                     "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": round(t_e2e, 6), "unit": "s",
                 "h2d_bytes_per_step": int(bh.numel() * 16), "d2h_bytes_per_step": int(xh.numel() * 16)},
         "gpu_launches": int(launches_ms),

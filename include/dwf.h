@@ -169,7 +169,8 @@ dwf_status dwf_field_export(dwf_ctx *ctx, void *canon_out, int canon_is_fp32,
  *   dagger = 0:  out = -1/2 Dhop (M_phi in)            (M^4_eo or M^4_oe)
  *   dagger = 1:  out = -1/2 M_phi^+ Dhop^+ in          ((M^4)^+)
  * `in` lives on parity 1 - out_parity, `out` on out_parity (0 even, 1 odd).
- * prec: DWF_FP64 or DWF_FP32 (native fields). out must not alias in. */
+ * prec: any (native fields; FP16/BF16 use FP16 links and FP32 arithmetic and
+ * store the result with a new per-(site, s) scale). out must not alias in. */
 dwf_status dwf_dslash_eo(dwf_ctx *ctx, void *out, const void *in, int out_parity,
                          int dagger, dwf_prec prec, int nrhs, const double *mf,
                          void *stream);

@@ -171,7 +171,7 @@ dwf_status dwf_dslash_eo(dwf_ctx *ctx, void *out, const void *in, int out_parity
                          dwf_prec prec, int nrhs, const double *mf, void *stream) {
   API_TRY(ctx)
   check_common(ctx, nrhs, mf);
-  check_prec_op(prec);
+  DWF_REQUIRE(prec >= DWF_FP64 && prec <= DWF_BF16, DWF_ERR_INVALID_ARG, "unknown precision");
   DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
   DWF_REQUIRE(out_parity == 0 || out_parity == 1, DWF_ERR_INVALID_ARG, "parity must be 0 or 1");
   DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");

@@ -20,7 +20,10 @@ from paper_1811_08488_gb300 import synthetic as syn
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5,
+       # FP16/BF16: input and output rounded to 11 / 8 bits of their (site, s)
+       # maximum, links to FP16: about 3 roundings of 2^-11 / 2^-8
+       "fp16": 3e-3, "bf16": 2.5e-2}
 
 
 def dwf():
@@ -85,7 +88,7 @@ def test_import_export_roundtrip(prec):
 
 
 @pytest.mark.parametrize("dims,Ls,kw", SHAPES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_dslash_eo(dims, Ls, kw, prec, dagger):
     S = Setup(dims, Ls, **kw)
