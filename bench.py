@@ -349,6 +349,103 @@ def run_gpu(args, rank, world, dist):
     return res, info_ms, nblocks
 
 
+# ----------------------------------------------------------------------------
+# studies: the solver parameter sweeps (one JSON line per configuration)
+# ----------------------------------------------------------------------------
+def _divisor_blocks(dims, cands):
+    return [b for b in cands if all(d % x == 0 and x % 2 == 0 for d, x in zip(dims, b))]
+
+
+STUDY_BLOCKS = [(4, 4, 4, 4), (6, 6, 6, 8), (8, 8, 8, 8), (8, 8, 8, 16), (12, 12, 12, 8),
+                (12, 12, 12, 16), (16, 16, 16, 16)]
+
+
+def run_study(args):
+    """Time MSPCG / plain CG solves of one workload over a parameter sweep.
+
+    k      inner iterations k in {0 (plain CG), 2, 3, 4, 6, 8, 12}
+    snake  block operator with and without the snake terms (k = 6), and plain CG
+    inner  inner storage FP32 / FP16 / BF16 (k = 6), and plain CG
+    block  every block shape of STUDY_BLOCKS that tiles the lattice (k = 6)
+    rhs    all right-hand sides of the workload in one call vs one call each
+    Each configuration: one short untimed solve (plans, graphs), then
+    `--steps` timed solves (CUDA events, L2 flushed before each). With
+    `--maxiter` the solves stop after that many outer iterations and the
+    line reports the time per outer iteration and the residual reached.
+    """
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    torch.cuda.set_device(0)
+    name = args.workload
+    w = syn.WORKLOADS[name]
+    dims, Ls = w["dims"], w["Ls"]
+    U, srcs = syn.workload_inputs(name)
+    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"])
+    ctx.gauge_load(U)
+    masses = list(w["mf"])
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    b_all = torch.from_numpy(np.ascontiguousarray(np.stack(srcs))).cuda()
+    base = dict(block=w["block"], inner="fp16", outer="fp32", inner_iters=6, tol=1e-10)
+    if args.maxiter:
+        base["maxiter"] = args.maxiter
+
+    configs = []
+    if args.study == "k":
+        configs = [dict(base, inner_iters=k) for k in (0, 2, 3, 4, 6, 8, 12)]
+    elif args.study == "snake":
+        configs = [dict(base, inner_iters=0)] + [dict(base, snake=s) for s in (1, 0)]
+    elif args.study == "inner":
+        configs = [dict(base, inner_iters=0)] + [dict(base, inner=p) for p in ("fp32", "fp16", "bf16")]
+    elif args.study == "block":
+        configs = [dict(base, block=bl) for bl in _divisor_blocks(dims, STUDY_BLOCKS)]
+    elif args.study == "rhs":
+        configs = [dict(base, _batched=True), dict(base, _batched=False)]
+    else:
+        raise SystemExit(f"unknown study {args.study}")
+
+    def solve_once(prm_kw, b, mf, timed):
+        kw = {k: v for k, v in prm_kw.items() if not k.startswith("_")}
+        prm = dwf.default_params(**kw)
+        x = torch.zeros_like(b)
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = ctx.solve(x, b, mf, prm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3, st, info
+
+    for cfg in configs:
+        warm = dict(cfg, maxiter=2)
+        if cfg.get("_batched", True):
+            calls = [(b_all, masses)]
+        else:
+            calls = [(b_all[i:i + 1], [m]) for i, m in enumerate(masses)]
+        solve_once(warm, *calls[0], False)
+        for _ in range(args.steps):
+            t_tot, infos, sts = 0.0, [], []
+            for b, mf in calls:
+                t, st, info = solve_once(cfg, b, mf, True)
+                t_tot += t
+                infos += info
+                sts.append(st)
+            outer = [i["outer_iters"] for i in infos]
+            line = {"study": args.study, "workload": name,
+                    "inner_iters": cfg["inner_iters"], "inner": cfg["inner"],
+                    "block": "x".join(map(str, cfg["block"])), "snake": cfg.get("snake", 1),
+                    "nrhs": len(masses), "one_call": cfg.get("_batched", True),
+                    "seconds": round(t_tot, 4), "status": sts,
+                    "outer_iters": outer, "max_outer_iters": max(outer),
+                    "reliable_updates": [i["reliable_updates"] for i in infos],
+                    "true_resid": [float(f"{i['true_resid']:.3e}") for i in infos],
+                    "converged": all(i["converged"] for i in infos)}
+            if args.maxiter:
+                line["s_per_outer_iter"] = round(t_tot / max(1, max(outer)), 6)
+            print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,7 +455,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dslash-only", action="store_true",
                     help="time only the FP32 hop kernel (used for kernel profiles)")
+    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs"],
+                    help="solver parameter sweep instead of the benchmark line")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
+    ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")
     args = ap.parse_args()
+    if args.study:
+        run_study(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 
