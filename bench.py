@@ -228,6 +228,45 @@ def run_gpu(args, rank, world, dist):
         e1.synchronize()
         times16.append(e0.elapsed_time(e1) * 1e-3)
     t_hop16 = statistics.median(times16)
+
+    def time_call(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush_l2(l2_flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts)
+
+    # --- M_5^-1 on the tensor cores, 16 right-hand sides (the multi-RHS shape) ---
+    m5 = None
+    if not args.dslash_only:
+        nr = 16
+        m16 = list(syn.log_spaced_masses(0.001, 0.05, nr))
+        canon16 = canon.expand(nr, *canon.shape[1:]).contiguous()
+        peak_m5, _ = peaks()
+        m5 = {"nrhs": nr, "note": "call time: kernel + 4-byte status read + stream sync"}
+        for prec, bpe in (("fp32", 96), ("fp16", 52)):
+            fi, fo = ctx.new_field(prec, nr), ctx.new_field(prec, nr)
+            ctx.field_import(fi, prec, canon16, nr)
+            t = time_call(lambda: ctx.m5inv_gemm(fo, fi, 0, prec, m16))
+            alg = 2 * Vh * Ls * bpe * nr
+            m5[prec] = {"us": round(t * 1e6, 1), "alg_bytes": alg, "gbs": round(alg / t / 1e9, 1),
+                        "frac": round(alg / t / 1e9 / peak_m5, 4)}
+            if prec == "fp32":
+                t_cc = time_call(lambda: ctx.m5inv(fo, fi, 0, "fp32", m16))
+                m5["closed_form_fp32"] = {"kernel": "ls_kernel (CUDA cores)",
+                                          "us": round(t_cc * 1e6, 1),
+                                          "gbs": round(alg / t_cc / 1e9, 1)}
+            del fi, fo
+        del canon16
+        torch.cuda.empty_cache()
+
     if args.dslash_only:
         times_dag = []
         for _ in range(30):
@@ -332,6 +371,7 @@ def run_gpu(args, rank, world, dist):
         "dslash": {"kernel": "hop2_kernel<F32,DAG=0,PRE=1> (M^4 = -1/2 Dhop M_phi)",
                    "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
                    "gbs": round(hop_gbs, 1), "frac_of_8tbs_nominal": round(hop_gbs / 8000, 4)},
+        "m5inv_gemm": m5,
         "dslash_fp16_dagger": {"kernel": "hop2_kernel<F16,DAG=1,PRE=0>", "us": round(t_hop16 * 1e6, 2),
                                "alg_bytes": alg16, "gbs": round(alg16 / t_hop16 / 1e9, 1),
                                "frac": round(alg16 / t_hop16 / 1e9 / peak, 4)},

@@ -105,7 +105,8 @@ typedef struct {
   double tol;         /* stop when |b - A x| / |b| <= tol (recomputed residual) */
   int maxiter;        /* maximum outer iterations                               */
   int inner_iters;    /* k fixed inner CG iterations per block; 0 = plain CG    */
-  int block[4];       /* sub-lattice extents (even, dividing dims)              */
+  int block[4];       /* sub-lattice extents (even, dividing dims); all zero:   
+                       * the block autotuner's shape (dwf_autotune_block)     */
   dwf_prec outer;     /* DWF_FP64 or DWF_FP32 (FP32: FP64 reliable updates)     */
   dwf_prec inner;     /* DWF_FP32, DWF_FP16 or DWF_BF16 block-solve storage     */
   double delta;       /* reliable update when |r| < delta * max|r| since last   */
@@ -186,6 +187,23 @@ dwf_status dwf_m5(dwf_ctx *ctx, void *out, const void *in, int dagger,
 dwf_status dwf_m5inv(dwf_ctx *ctx, void *out, const void *in, int dagger,
                      dwf_prec prec, int nrhs, const double *mf, void *stream);
 
+/* out = M_5^-1 in (dagger = 0) or M_5^-+ in (dagger = 1), the same operator as
+ * dwf_m5inv (paper Sec. 2.2, eq. (dirac_equation)), computed as a dense real
+ * GEMM on the tensor cores: per chirality, the Ls x Ls matrix M_5^-1 (built
+ * and inverted on the host in FP64 for each right-hand side's m_f) times the
+ * Ls-vectors of every (site, spin, colour, re/im), all right-hand sides in
+ * one launch. prec: DWF_FP32 (operands split into two FP16 parts, result to
+ * about 1e-6 relative), DWF_FP16 or DWF_BF16 (result at the storage's own
+ * precision). Any Ls a context takes (<= DWF_MAX_LS = 32: one or two K steps
+ * of 16). Fields in the native layout (dwf_field_import);
+ * `out` and `in` may not overlap. The call returns after its work on
+ * `stream` has finished (it reads the kernel's status word). Uses a small
+ * context-owned device buffer, so calls on one context must not overlap.
+ * Errors: INVALID_ARG, UNSUPPORTED (FP64 fields), TIMEOUT (a
+ * bounded device wait expired), CUDA. */
+dwf_status dwf_m5inv_gemm(dwf_ctx *ctx, void *out, const void *in, int dagger,
+                          dwf_prec prec, int nrhs, const double *mf, void *stream);
+
 /* out = D_PC in (dagger = 0) or D_PC^+ in (dagger = 1), even parity fields
  * (paper eq. (dirac_equation)). */
 dwf_status dwf_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger,
@@ -229,6 +247,26 @@ dwf_status dwf_block_apply(dwf_ctx *ctx, void *out, const void *in,
 dwf_status dwf_block_precond(dwf_ctx *ctx, void *z, const void *r,
                              const dwf_solver_params *params, int nrhs,
                              const double *mf, void *stream);
+
+/* Block-shape autotuner for the multisplitting preconditioner (the blocks of
+ * paper Sec. 2.4). Candidates: b^3 x bt blocks, b in {4, 6, 8, 12, 16}, bt in
+ * {4, 6, 8, 12, 16, 24, 32} with b/2 <= bt <= 2b, dividing the lattice, at
+ * least two blocks. Each candidate runs one untimed outer iteration and then
+ * `trial` (>= 2) timed outer iterations of mspcg_solve on the sources b (as in
+ * mspcg_solve: canonical even fields, host pointers when params->io_on_host)
+ * with params' other settings; the time to params->tol is predicted from the
+ * time per iteration and the rate at which the largest true residual fell.
+ * The fastest shape is written to block_out[4], its predicted time to
+ * *predicted_seconds (if not null), and remembered in the context, so that
+ * mspcg_solve with params->block all zero and the same parameters, masses
+ * and nrhs uses it without tuning again (with no remembered shape it tunes
+ * first, trial = 20). The other candidates' block plans are released.
+ * Synchronous. Errors: INVALID_ARG (inner_iters == 0, trial < 2), NO_GAUGE,
+ * UNSUPPORTED (no candidate tiles the lattice), NOT_CONVERGED (no candidate
+ * reduced the residual), CUDA. */
+dwf_status dwf_autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const double *mf,
+                              const dwf_solver_params *params, int trial, int block_out[4],
+                              double *predicted_seconds, void *stream);
 
 /* Solve D_PC^+ D_PC x = b for nrhs right-hand sides with Algorithm 1 (MSPCG;
  * plain CG when params->inner_iters == 0). x and b are canonical complex128

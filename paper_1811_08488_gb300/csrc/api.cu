@@ -205,6 +205,17 @@ dwf_status dwf_m5inv(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_pr
   return ls_entry(ctx, out, in, dagger, prec, nrhs, mf, stream, true);
 }
 
+dwf_status dwf_m5inv_gemm(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec,
+                          int nrhs, const double *mf, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  DWF_REQUIRE(prec >= DWF_FP64 && prec <= DWF_BF16, DWF_ERR_INVALID_ARG, "unknown precision");
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  dwf::launch_m5inv_gemm(ctx, prec, (char *)out, (const char *)in, dagger ? 1 : 0, nrhs, mf,
+                         (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
 dwf_status dwf_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec, int nrhs,
                    const double *mf, void *stream) {
   API_TRY(ctx)
@@ -266,6 +277,20 @@ dwf_status dwf_block_precond(dwf_ctx *ctx, void *z, const void *r,
   API_CATCH(ctx)
 }
 
+dwf_status dwf_autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const double *mf,
+                              const dwf_solver_params *params, int trial, int block_out[4],
+                              double *predicted_seconds, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_params(params);
+  DWF_REQUIRE(b && block_out, DWF_ERR_INVALID_ARG, "null b or block_out");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->own_stream;
+  if (!stream) DWF_CUDA_TRY(cudaDeviceSynchronize());
+  dwf::autotune_block(ctx, b, nrhs, mf, params, trial, block_out, predicted_seconds, st);
+  API_CATCH(ctx)
+}
+
 dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
                        const dwf_solver_params *params, dwf_solve_info *info, void *stream) {
   API_TRY(ctx)
@@ -278,7 +303,19 @@ dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const dou
               "delta must be in (0, 1)");
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->own_stream;
   if (!stream) DWF_CUDA_TRY(cudaDeviceSynchronize());
-  dwf_status s = dwf::solve(ctx, x, b, nrhs, mf, params, info, st);
+  dwf_solver_params p = *params;
+  if (p.inner_iters > 0 && !p.block[0] && !p.block[1] && !p.block[2] && !p.block[3]) {
+    // block = {0, 0, 0, 0}: the autotuner's shape for these parameters
+    auto it = ctx->tuned_blocks.find(dwf::tune_key(&p, nrhs, mf));
+    if (it == ctx->tuned_blocks.end()) {
+      int blk[4];
+      dwf::autotune_block(ctx, b, nrhs, mf, &p, 20, blk, nullptr, st);
+      for (int i = 0; i < 4; ++i) p.block[i] = blk[i];
+    } else {
+      for (int i = 0; i < 4; ++i) p.block[i] = it->second[i];
+    }
+  }
+  dwf_status s = dwf::solve(ctx, x, b, nrhs, mf, &p, info, st);
   if (s != DWF_OK) {
     ctx->last_error = s == DWF_ERR_NOT_CONVERGED ? "not converged within maxiter"
                       : s == DWF_ERR_NAN         ? "NaN or Inf in a solver scalar"

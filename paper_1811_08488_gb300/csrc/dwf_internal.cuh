@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <map>
 #include <memory>
 #include <string>
@@ -233,8 +234,12 @@ struct dwf_ctx {
   // operator work buffers (odd/even temporaries, per precision)
   dwf::DevBuf tmp[4];
   dwf::DevBuf red;  // reduction partials and counters for operator calls
+  dwf::DevBuf tc_aux;  // tensor-core M_5^-1: status word and B operands
+  std::vector<double> tc_key;         // masses + adjoint flag of the B operands in tc_aux
+  float tc_unscale[DWF_MAX_RHS][2]{};  // their power-of-two scales
   std::map<std::string, std::unique_ptr<dwf::BlockPlan>> block_plans;
   std::map<std::string, std::unique_ptr<dwf::SolverPlan>> solver_plans;
+  std::map<std::string, std::array<int, 4>> tuned_blocks;  // autotuner results
   ~dwf_ctx();
 };
 
@@ -247,6 +252,9 @@ int hop_sites_per_cta(int Ls, dwf_prec p);
 size_t hop_smem_bytes(int Ls, dwf_prec p, int epi, int has_x);
 
 // ls.cu: Ls-local operators (M_5, M_5^-1) on native fields
+// Tensor-core M_5^-1 (csrc/m5tc.cu); synchronises `st` and checks the status word.
+void launch_m5inv_gemm(dwf_ctx *ctx, dwf_prec p, char *out, const char *in, int dagger, int nrhs,
+                       const double *mf, cudaStream_t st);
 void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride,
                   int nsite, int Ls, int dagger, int inv, int nrhs, const LsCoef *coef,
                   cudaStream_t st);

@@ -79,6 +79,13 @@ struct SolverPlan {
 dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
                  const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st);
 
+// Block-shape autotuner (csrc/autotune.cu).
+std::vector<std::array<int, 4>> block_candidates(const int dims[4]);
+std::string tune_key(const dwf_solver_params *p, int nrhs, const double *mf);
+void autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const double *mf,
+                    const dwf_solver_params *prm, int trial, int block_out[4],
+                    double *predicted, cudaStream_t st);
+
 void prepare_kernels();
 
 }  // namespace dwf

@@ -28,9 +28,9 @@ NOALLOC_SCRATCH_BYTES = 24 << 20
 # Every symbol include/dwf.h declares.
 EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_default",
            "dwf_gauge_load", "dwf_field_bytes", "dwf_field_import", "dwf_field_export",
-           "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_mpc", "dwf_mdagm", "dwf_mdagm_noalloc",
+           "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_m5inv_gemm", "dwf_mpc", "dwf_mdagm", "dwf_mdagm_noalloc",
            "dwf_block_apply",
-           "dwf_block_precond", "mspcg_solve"]
+           "dwf_block_precond", "dwf_autotune_block", "mspcg_solve"]
 
 
 class DwfError(RuntimeError):
@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_dslash_eo": (I, [P, P, P, I, I, I, I, D, P]),
         "dwf_m5": (I, [P, P, P, I, I, I, D, P]),
         "dwf_m5inv": (I, [P, P, P, I, I, I, D, P]),
+        "dwf_m5inv_gemm": (I, [P, P, P, I, I, I, D, P]),
+        "dwf_autotune_block": (I, [P, P, I, D, C.POINTER(SolverParams), I, C.POINTER(C.c_int), D, P]),
         "dwf_mpc": (I, [P, P, P, I, I, I, D, P]),
         "dwf_mdagm": (I, [P, P, P, I, I, D, P]),
         "dwf_mdagm_noalloc": (I, [P, P, P, I, I, D, P]),
@@ -218,6 +220,14 @@ class Context:
         self._check(lib().dwf_m5inv(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
                                     int(dagger), PREC.get(prec, prec), m.size, mp, _stream(stream)))
 
+    def m5inv_gemm(self, out, inp, dagger, prec, mf, stream=None):
+        """dwf_m5inv_gemm: M_5^-1 (dagger: its adjoint) on the tensor cores,
+        all right-hand sides of `mf` in one launch."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_m5inv_gemm(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
+                                         int(dagger), PREC.get(prec, prec), m.size, mp,
+                                         _stream(stream)))
+
     def mpc(self, out, inp, dagger, prec, mf, stream=None):
         m, mp = _masses(mf)
         self._check(lib().dwf_mpc(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)), int(dagger),
@@ -246,6 +256,16 @@ class Context:
                                             C.byref(params), m.size, mp, _stream(stream)))
 
     # ------------------------------------------------------------------- solve
+    def autotune_block(self, b, mf, params, trial=20, stream=None):
+        """dwf_autotune_block: returns (block shape, predicted seconds)."""
+        m, mp = _masses(mf)
+        blk = (C.c_int * 4)()
+        pred = C.c_double(0.0)
+        bp = b.ctypes.data if isinstance(b, np.ndarray) else _ptr(b)
+        self._check(lib().dwf_autotune_block(self._h, C.c_void_p(bp), m.size, mp, C.byref(params),
+                                             int(trial), blk, C.byref(pred), _stream(stream)))
+        return tuple(blk), pred.value
+
     def solve(self, x, b, mf, params, stream=None, raise_on_error=True):
         """mspcg_solve. x, b: canonical complex128 even fields (device tensors,
         or host numpy/pinned tensors with params.io_on_host = 1).
