@@ -246,7 +246,7 @@ def run_gpu(args, rank, world, dist):
     # --- M_5^-1 on the tensor cores, 16 right-hand sides (the multi-RHS shape) ---
     m5 = None
     if not args.dslash_only:
-        nr = 16
+        nr = args.m5_rhs
         m16 = list(syn.log_spaced_masses(0.001, 0.05, nr))
         canon16 = canon.expand(nr, *canon.shape[1:]).contiguous()
         peak_m5, _ = peaks()
@@ -266,6 +266,9 @@ def run_gpu(args, rank, world, dist):
             del fi, fo
         del canon16
         torch.cuda.empty_cache()
+        if args.m5_only:
+            return {"metric": "M_5^-1 GEMM HBM GB/s", "m5inv_gemm": m5,
+                    "config": {"workload": WORKLOAD, "nrhs": nr}}, None, None
 
     if args.dslash_only:
         times_dag = []
@@ -408,6 +411,7 @@ def run_study(args):
     inner  inner storage FP32 / FP16 / BF16 (k = 6), and plain CG
     block  every block shape of STUDY_BLOCKS that tiles the lattice (k = 6)
     rhs    all right-hand sides of the workload in one call vs one call each
+    pair   plain CG and MSPCG (k = 6) with the workload's block shape
     Each configuration: one short untimed solve (plans, graphs), then
     `--steps` timed solves (CUDA events, L2 flushed before each). With
     `--maxiter` the solves stop after that many outer iterations and the
@@ -441,6 +445,8 @@ def run_study(args):
         configs = [dict(base, block=bl) for bl in _divisor_blocks(dims, STUDY_BLOCKS)]
     elif args.study == "rhs":
         configs = [dict(base, _batched=True), dict(base, _batched=False)]
+    elif args.study == "pair":
+        configs = [dict(base, inner_iters=0), dict(base)]
     else:
         raise SystemExit(f"unknown study {args.study}")
 
@@ -495,7 +501,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dslash-only", action="store_true",
                     help="time only the FP32 hop kernel (used for kernel profiles)")
-    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs"],
+    ap.add_argument("--m5-only", action="store_true",
+                    help="time only the tensor-core M_5^-1 (used for kernel profiles)")
+    ap.add_argument("--m5-rhs", type=int, default=16, help="right-hand sides of the M_5^-1 timing")
+    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair"],
                     help="solver parameter sweep instead of the benchmark line")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
     ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")
@@ -539,7 +548,7 @@ def main():
         dist = td
     res, info_ms, nblocks = run_gpu(args, rank, world, dist)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and not args.dslash_only:
+        if world == 1 and not args.no_cpu_baseline and not args.dslash_only and not args.m5_only:
             s, cores = cpu_sample_1core(info_ms["outer_iters"], 6, nblocks)
             res["cpu_baseline"] = {"value": round(s["value"], 3), "unit": "s",
                                    "cores": cores, "kind": "oracle", "sample": s["sample"]}
