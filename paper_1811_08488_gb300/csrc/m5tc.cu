@@ -128,23 +128,43 @@ __host__ __device__ constexpr int tc_cols() {
   return kTcTiles * LP <= 128 ? 128 : 256;
 }
 
+// The A operands are written item by item: an item is 8 consecutive s (one
+// K group kg) of one 16-byte chunk c (4 reals r = 4(c % 3) .. +3 of chirality
+// c / 3) of one site h. The 3 KG items of a (site, chirality) slab sit in one
+// aligned group of G lanes, so the slab maximum is a G-lane shuffle reduction.
+template <int LP>
+struct TcShape {
+  static constexpr int KG = LP / 8;                        // K groups per row
+  static constexpr int G = (3 * KG <= 8) ? 8 : 16;         // lanes per slab
+  static constexpr int kSlabsPerRound = kTcThreads / G;    // slabs handled at once
+  static constexpr int kRounds = 2 * kTcSites / kSlabsPerRound;
+};
+
+// Bytes of the shared region that holds the A operands and, once the MMAs
+// are done, the FP32 output staging [chunk][site][s][4] (chunks padded by 16 B).
+template <int LP, bool SPLIT>
+__host__ __device__ inline int tc_region_bytes(int Ls) {
+  const int a = (SPLIT ? 2 : 1) * kTcTiles * 128 * LP * 2;
+  const int stg = 6 * (kTcSites * Ls * 4 + 4) * 4;
+  const int r = a > stg ? a : stg;
+  return (r + 127) / 128 * 128;
+}
+
 template <class S, int LP, bool SPLIT>
-__global__ void __launch_bounds__(kTcThreads) m5inv_gemm_kernel(const __grid_constant__ TcParams P) {
+__global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr int NA = SPLIT ? 2 : 1;           // A terms (hi, lo)
+  using SH = TcShape<LP>;
   constexpr int kTileBytes = 128 * LP * 2;    // one M = 128 tile, K = LP FP16
   constexpr int kABytes = kTcTiles * kTileBytes;
   constexpr int kBImg = LP * LP * 2;          // one N x K image
-  constexpr int KG = LP / 8;                  // 16-byte K groups per row
   constexpr uint32_t kCols = tc_cols<LP>();
   const int Ls = P.Ls;
   const int chs = kTcSites * Ls * 4 + 4;      // staging floats per chunk (padded)
 
   unsigned char *A = smem;
-  unsigned char *B = A + NA * kABytes;
-  float *stg = reinterpret_cast<float *>(B + 4 * kBImg);
-  float *sig = stg + 6 * chs;                 // [site][chi]: 2^-e, then 2^e
-  float *sig_inv = sig + 2 * kTcSites;
+  float *stg = reinterpret_cast<float *>(smem);
+  unsigned char *B = smem + tc_region_bytes<LP, SPLIT>(Ls);
+  float *sig_inv = reinterpret_cast<float *>(B + 4 * kBImg);  // [site][chi]: 2^e
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sig_inv + 2 * kTcSites);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
 
@@ -167,88 +187,86 @@ __global__ void __launch_bounds__(kTcThreads) m5inv_gemm_kernel(const __grid_con
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-
   // B operands of this right-hand side (four images: chi x {hi, lo})
   {
     const uint4 *src = P.bimg + (size_t)rhs * (4 * kBImg / 16);
     uint4 *dst = reinterpret_cast<uint4 *>(B);
     for (int i = tid; i < 4 * kBImg / 16; i += kTcThreads) dst[i] = __ldg(src + i);
   }
-  // input -> staging, FP32 values, [chunk c][site h][s][4]
-  if constexpr (std::is_same<S, F32>::value) {
-    const int n4 = nh * Ls;
-    const float4 *src = reinterpret_cast<const float4 *>(ip) + (size_t)h0 * Ls;
-    for (int c = 0; c < 6; ++c)
-      for (int e = tid; e < n4; e += kTcThreads)
-        *reinterpret_cast<float4 *>(stg + c * chs + e * 4) = __ldg(src + (size_t)c * cs + e);
-  } else {
-    for (int e = tid; e < nh * Ls; e += kTcThreads) {
-      float v[24];
-      load24<S>(ip, P.soff, cs, h0 * Ls + e, v);
-#pragma unroll
-      for (int c = 0; c < 6; ++c)
-        *reinterpret_cast<float4 *>(stg + c * chs + e * 4) =
-            make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-    }
-  }
-  __syncthreads();
 
-  // power-of-two scale per (site, chirality): 64 groups of 4 threads
-  {
-    const int g = tid >> 2, q = tid & 3, h = g >> 1, chi = g & 1;
+  // A operands, canonical K-major layout without swizzle: row m of tile t,
+  // K group kg (8 FP16 = 16 bytes) at t*kTileBytes + (m/8)*(LP*16) + kg*128 + (m%8)*16.
+#pragma unroll 1
+  for (int round = 0; round < SH::kRounds; ++round) {
+    const int g = round * SH::kSlabsPerRound + tid / SH::G;  // slab = 2 h + chi
+    const int li = tid % SH::G;
+    const int h = g >> 1, chi = g & 1;
+    const bool item = li < 3 * SH::KG;
+    const int cc = item ? li / SH::KG : 0, kg = item ? li % SH::KG : 0;
+    const int c = chi * 3 + cc;
+    float4 v[8];
     float m = 0.f;
-    if (h < nh) {
-      for (int idx = q; idx < 3 * Ls; idx += 4) {
-        const int cc = idx / Ls, s = idx - cc * Ls;
-        const float4 v =
-            *reinterpret_cast<const float4 *>(stg + (chi * 3 + cc) * chs + (h * Ls + s) * 4);
-        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (item && h < nh) {
+      const int e0 = (h0 + h) * Ls + kg * 8;
+      if constexpr (std::is_same<S, F32>::value) {
+        const float4 *src = reinterpret_cast<const float4 *>(ip) + (size_t)c * cs + e0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (kg * 8 + q < Ls) v[q] = __ldg(src + q);
+      } else {
+        // FP16/BF16: reals 4c .. 4c+3 are halves 4(c % 2) .. +3 of chunk c / 2
+        const uint4 *src = reinterpret_cast<const uint4 *>(ip) + (size_t)(c >> 1) * cs + e0;
+        const float *scl = reinterpret_cast<const float *>(ip + P.soff) + e0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (kg * 8 + q < Ls) {
+            float w[8];
+            unpack8<S>(__ldg(src + q), w);
+            const float f = __ldg(scl + q);
+            const int o = (c & 1) * 4;
+            v[q] = make_float4(w[o] * f, w[o + 1] * f, w[o + 2] * f, w[o + 3] * f);
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+    }
+#pragma unroll
+    for (int o = 1; o < SH::G; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // m = f 2^e with f in [0.5, 1): the scaled slab has its maximum in [0.5, 1)
+    const int ex = (m > 0.f && m < INFINITY) ? ((__float_as_int(m) >> 23) & 0xFF) - 126 : 0;
+    const float sc = pow2f(-ex);
+    if (li == 0) sig_inv[g] = pow2f(ex);
+    if (item) {
+      const int rho0 = h * 12 + 4 * cc;  // first row of the item within its chirality
+      const int t = chi * 3 + rho0 / 128, m0 = rho0 % 128;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 w = v[q];
+          x[q] = (j == 0 ? w.x : j == 1 ? w.y : j == 2 ? w.z : w.w) * sc;
+        }
+        uint4 hi, lo;
+        __half2 *ph = reinterpret_cast<__half2 *>(&hi), *pl = reinterpret_cast<__half2 *>(&lo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const __half2 a = __floats2half2_rn(x[2 * q], x[2 * q + 1]);
+          ph[q] = a;
+          if (SPLIT) {
+            const float2 af = __half22float2(a);
+            pl[q] = __floats2half2_rn(x[2 * q] - af.x, x[2 * q + 1] - af.y);
+          }
+        }
+        const int mm = m0 + j;
+        const int off = t * kTileBytes + (mm >> 3) * (LP * 16) + kg * 128 + (mm & 7) * 16;
+        *reinterpret_cast<uint4 *>(A + off) = hi;
+        if (SPLIT) *reinterpret_cast<uint4 *>(A + kABytes + off) = lo;
       }
     }
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    if (q == 0) {
-      // m = f 2^e with f in [0.5, 1): the scaled slab has its maximum in [0.5, 1)
-      const int e = (m > 0.f && m < INFINITY) ? ((__float_as_int(m) >> 23) & 0xFF) - 126 : 0;
-      sig[g] = pow2f(-e);
-      sig_inv[g] = pow2f(e);
-    }
-  }
-  __syncthreads();
-
-  // A operands: canonical K-major layout without swizzle. Row m of tile t,
-  // K group jk (8 FP16 = 16 bytes) at t*kTileBytes + (m/8)*(LP*16) + jk*128 + (m%8)*16.
-  for (int task = tid; task < kTcTiles * 128 * KG; task += kTcThreads) {
-    const int m = task & 127, rest = task >> 7;
-    const int jk = rest % KG, t = rest / KG;
-    const int chi = t / 3, rho = (t % 3) * 128 + m, h = rho / 12, r = rho - h * 12;
-    const int c = chi * 3 + (r >> 2), j = r & 3;
-    float x[8];
-    if (h < nh) {
-      const float sc = sig[h * 2 + chi];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int s = jk * 8 + q;
-        x[q] = s < Ls ? stg[c * chs + (h * Ls + s) * 4 + j] * sc : 0.f;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = 0.f;
-    }
-    uint4 hi, lo;
-    __half2 *ph = reinterpret_cast<__half2 *>(&hi), *pl = reinterpret_cast<__half2 *>(&lo);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const __half2 a = __floats2half2_rn(x[2 * q], x[2 * q + 1]);
-      ph[q] = a;
-      if (SPLIT) {
-        const float2 af = __half22float2(a);
-        pl[q] = __floats2half2_rn(x[2 * q] - af.x, x[2 * q + 1] - af.y);
-      }
-    }
-    const int off = t * kTileBytes + (m >> 3) * (LP * 16) + jk * 128 + (m & 7) * 16;
-    *reinterpret_cast<uint4 *>(A + off) = hi;
-    if (SPLIT) *reinterpret_cast<uint4 *>(A + kABytes + off) = lo;
   }
 
   // make the generic-proxy smem writes visible to the tensor core, then issue
@@ -285,7 +303,8 @@ __global__ void __launch_bounds__(kTcThreads) m5inv_gemm_kernel(const __grid_con
   if (!ok && tid == 0) atomicExch(P.status, 1);
 
   if (ok) {
-    // TMEM -> staging: warp w reads lanes 32 (w % 4) .. +31 of tiles t = w/4, w/4 + 2, ...
+    // TMEM -> staging (the A region is free once the MMAs completed): warp w
+    // reads lanes 32 (w % 4) .. +31 of tiles t = w/4, w/4 + 2, ...
     const int sub = warp & 3;
     for (int t = warp >> 2; t < kTcTiles; t += 2) {
       uint32_t d[LP];
@@ -302,39 +321,45 @@ __global__ void __launch_bounds__(kTcThreads) m5inv_gemm_kernel(const __grid_con
       }
     }
   }
-  __syncthreads();
-  if (ok) {
-    if constexpr (std::is_same<S, F32>::value) {
-      const int n4 = nh * Ls;
-      float4 *dst = reinterpret_cast<float4 *>(op) + (size_t)h0 * Ls;
-      for (int c = 0; c < 6; ++c)
-        for (int e = tid; e < n4; e += kTcThreads)
-          dst[(size_t)c * cs + e] = *reinterpret_cast<const float4 *>(stg + c * chs + e * 4);
-    } else {
-      for (int e = tid; e < nh * Ls; e += kTcThreads) {
-        float v[24];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const float4 q = *reinterpret_cast<const float4 *>(stg + c * chs + e * 4);
-          v[4 * c] = q.x; v[4 * c + 1] = q.y; v[4 * c + 2] = q.z; v[4 * c + 3] = q.w;
-        }
-        store24<S>(op, P.soff, cs, h0 * Ls + e, v);
-      }
-    }
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if constexpr (std::is_same<S, F32>::value) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols)
                  : "memory");
+  if (!ok) return;
+  if constexpr (std::is_same<S, F32>::value) {
+    // each chunk's sites are one contiguous run in global memory: bulk copies
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)nh * Ls * 16;
+      for (int c = 0; c < 6; ++c) {
+        char *dst = op + ((size_t)c * cs + (size_t)h0 * Ls) * 16;
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                     "r"(smem_u32(stg + c * chs)), "r"(bytes)
+                     : "memory");
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+  } else {
+    for (int e = tid; e < nh * Ls; e += kTcThreads) {
+      float v[24];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float4 q = *reinterpret_cast<const float4 *>(stg + c * chs + e * 4);
+        v[4 * c] = q.x; v[4 * c + 1] = q.y; v[4 * c + 2] = q.z; v[4 * c + 3] = q.w;
+      }
+      store24<S>(op, P.soff, cs, h0 * Ls + e, v);
+    }
+  }
 }
 
 template <int LP, bool SPLIT>
 size_t tc_smem_bytes(int Ls) {
-  const size_t a = (size_t)(SPLIT ? 2 : 1) * kTcTiles * 128 * LP * 2;
   const size_t b = 4u * LP * LP * 2;
-  const size_t stg = 6u * (kTcSites * Ls * 4 + 4) * 4;
-  return a + b + stg + 4u * kTcSites * 4 + 16;
+  const size_t bytes = (size_t)tc_region_bytes<LP, SPLIT>(Ls) + b + 2u * kTcSites * 4 + 16;
+  // at least 48 KB: at most four CTAs (4 x 128 TMEM columns) share an SM
+  return bytes < 48u * 1024 ? 48u * 1024 : bytes;
 }
 
 // Dense M_5 of one chirality (Sec. 2.2): alpha on the diagonal, beta on the
