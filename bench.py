@@ -412,6 +412,7 @@ def run_study(args):
     block  every block shape of STUDY_BLOCKS that tiles the lattice (k = 6)
     rhs    all right-hand sides of the workload in one call vs one call each
     pair   plain CG and MSPCG (k = 6) with the workload's block shape
+    autotune  the block autotuner's pick, then the solve with block = 0
     Each configuration: one short untimed solve (plans, graphs), then
     `--steps` timed solves (CUDA events, L2 flushed before each). With
     `--maxiter` the solves stop after that many outer iterations and the
@@ -447,6 +448,27 @@ def run_study(args):
         configs = [dict(base, _batched=True), dict(base, _batched=False)]
     elif args.study == "pair":
         configs = [dict(base, inner_iters=0), dict(base)]
+    elif args.study == "autotune":
+        # the autotuner's pick (20 trial outer iterations per candidate), then
+        # the full solve with block = 0 (the remembered pick)
+        prm = dwf.default_params(**dict(base, block=(0, 0, 0, 0)))
+        t0 = time.perf_counter()
+        blk, pred = ctx.autotune_block(b_all, masses, prm, trial=20)
+        t_tune = time.perf_counter() - t0
+        x = torch.zeros_like(b_all)
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = ctx.solve(x, b_all, masses, prm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"study": "autotune", "workload": name, "block": "x".join(map(str, blk)),
+                          "tuning_seconds": round(t_tune, 3), "predicted_seconds": round(pred, 4),
+                          "seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "status": st,
+                          "outer_iters": [i["outer_iters"] for i in info],
+                          "converged": all(i["converged"] for i in info)}), flush=True)
+        return
     else:
         raise SystemExit(f"unknown study {args.study}")
 
@@ -504,7 +526,7 @@ def main():
     ap.add_argument("--m5-only", action="store_true",
                     help="time only the tensor-core M_5^-1 (used for kernel profiles)")
     ap.add_argument("--m5-rhs", type=int, default=16, help="right-hand sides of the M_5^-1 timing")
-    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair"],
+    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune"],
                     help="solver parameter sweep instead of the benchmark line")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
     ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")
