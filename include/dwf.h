@@ -98,6 +98,9 @@ typedef struct {
   double b, c;        /* Moebius coefficients (Shamir: b = 1, c = 0)         */
   double M5;          /* domain-wall height                                  */
   int t_antiperiodic; /* 1: antiperiodic in t (default), 0: periodic          */
+  int recon12;        /* 1: FP32/FP16 links keep their first two rows and a   
+                       * sign; the third row is rebuilt as the conjugate of   
+                       * the cross product (SU(3)); 0: all 18 reals (default) */
 } dwf_action;
 
 /* Solver parameters. Start from dwf_solver_params_default(). */

@@ -55,6 +55,8 @@ dwf_status dwf_create(dwf_ctx **out, int device, const dwf_action *a) {
       DWF_REQUIRE(a->dims[m] >= 2 && a->dims[m] % 2 == 0, DWF_ERR_INVALID_ARG,
                   "lattice extents must be even and >= 2");
     DWF_REQUIRE(a->Ls >= 2 && a->Ls <= DWF_MAX_LS, DWF_ERR_INVALID_ARG, "Ls out of range");
+    DWF_REQUIRE(a->recon12 == 0 || a->recon12 == 1, DWF_ERR_INVALID_ARG,
+                "recon12 must be 0 or 1");
     const double alpha = a->b * (4.0 - a->M5) + 1.0;
     DWF_REQUIRE(alpha != 0.0 && a->b == a->b && a->c == a->c, DWF_ERR_INVALID_ARG,
                 "M_5 is singular for these b, M5");
@@ -126,10 +128,11 @@ dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device) {
     src = tmp.as<double>();
   }
   const size_t nrec = (size_t)ctx->geo.V4 * 4;
-  ctx->links[0].ensure(nrec * 144);
-  ctx->links[1].ensure(nrec * 80);
-  ctx->links[2].ensure(nrec * 48);
-  dwf::launch_pack_links(src, ctx->links[0].c(), ctx->links[1].c(), ctx->links[2].c(),
+  const int rc = ctx->act.recon12;
+  ctx->links[0].ensure(nrec * dwf::link_record_bytes(DWF_FP64));
+  ctx->links[1].ensure(nrec * dwf::link_record_bytes(DWF_FP32, rc));
+  ctx->links[2].ensure(nrec * dwf::link_record_bytes(DWF_FP16, rc));
+  dwf::launch_pack_links(src, ctx->links[0].c(), ctx->links[1].c(), ctx->links[2].c(), rc,
                          ctx->act.dims, ctx->act.t_antiperiodic, nullptr);
   DWF_CUDA_TRY(cudaDeviceSynchronize());
   for (auto &kv : ctx->block_plans) kv.second->links_valid = false;

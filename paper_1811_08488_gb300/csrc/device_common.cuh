@@ -187,6 +187,22 @@ __device__ __forceinline__ void load24x2(const char *base, long long soff, int c
   }
 }
 
+// FP16/BF16: the stored values of elements e and e+1 (e even) without their
+// scales, which are returned in scl (the caller folds them in later).
+template <class S>
+__device__ __forceinline__ void load24x2_unscaled(const char *base, long long soff, int cs, int e,
+                                                  float *v0, float *v1, float2 &scl) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(base) + e;
+  scl = __ldg(reinterpret_cast<const float2 *>(base + soff) + e / 2);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint32_t a[8];
+    ldg256(p + (size_t)k * cs, a);
+    unpack8<S>(make_uint4(a[0], a[1], a[2], a[3]), v0 + 8 * k);
+    unpack8<S>(make_uint4(a[4], a[5], a[6], a[7]), v1 + 8 * k);
+  }
+}
+
 // Store the 24 reals of elements e (v0) and e+1 (v1); e even. FP16/BF16 store
 // each element relative to its own maximum.
 template <class S>
@@ -226,10 +242,30 @@ __device__ __forceinline__ void store24x2(char *base, long long soff, int cs, in
 // Link records: 18 reals of U[a][b] (row-major complex) per (owner, mu), in
 // kLinkChunks 16-byte words (FP64 9, FP32 5, FP16 3).
 // ---------------------------------------------------------------------------
+// Third row of a reconstruct-12 link: u[0..11] hold sg * (row 0, row 1) of an
+// SU(3) matrix, so sg * conj(row0 x row1) = sg * row 2 (the cross product of
+// the signed rows carries sg^2 = 1).
+template <class R>
+__device__ __forceinline__ void reconstruct_row2(R *u, R sg) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    const R ar = u[2 * a], ai = u[2 * a + 1], br = u[2 * b], bi = u[2 * b + 1];          // row 0
+    const R cr = u[6 + 2 * a], ci = u[6 + 2 * a + 1], dr = u[6 + 2 * b], di = u[6 + 2 * b + 1];  // row 1
+    // (row0 x row1)_c = row0_a row1_b - row0_b row1_a
+    const R re = (ar * dr - ai * di) - (br * cr - bi * ci);
+    const R im = (ar * di + ai * dr) - (br * ci + bi * cr);
+    u[12 + 2 * c] = sg * re;
+    u[12 + 2 * c + 1] = -sg * im;
+  }
+}
+
 // Load the link record whose word 0 is at w; word k is at w[k * ws] (the
-// chunk-major link layout: ws = number of link owners).
+// chunk-major link layout: ws = number of link owners). recon: the record
+// holds two rows and a sign (reconstruct-12, FP32/FP16/BF16 only).
 template <class S>
-__device__ __forceinline__ void load_link(const uint4 *w, size_t ws, typename S::R *u) {
+__device__ __forceinline__ void load_link(const uint4 *w, size_t ws, typename S::R *u,
+                                          int recon = 0) {
   if constexpr (std::is_same<S, F64>::value) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -237,19 +273,37 @@ __device__ __forceinline__ void load_link(const uint4 *w, size_t ws, typename S:
       u[2 * k] = q.x; u[2 * k + 1] = q.y;
     }
   } else if constexpr (std::is_same<S, F32>::value) {
+    if (recon) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float4 q = __ldg(reinterpret_cast<const float4 *>(w + k * ws));
-      u[4 * k] = q.x; u[4 * k + 1] = q.y; u[4 * k + 2] = q.z; u[4 * k + 3] = q.w;
+      for (int k = 0; k < 3; ++k) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(w + k * ws));
+        u[4 * k] = q.x; u[4 * k + 1] = q.y; u[4 * k + 2] = q.z; u[4 * k + 3] = q.w;
+      }
+      reconstruct_row2<float>(u, __ldg(reinterpret_cast<const float *>(w + 3 * ws)));
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(w + k * ws));
+        u[4 * k] = q.x; u[4 * k + 1] = q.y; u[4 * k + 2] = q.z; u[4 * k + 3] = q.w;
+      }
+      const float2 q = __ldg(reinterpret_cast<const float2 *>(w + 4 * ws));
+      u[16] = q.x; u[17] = q.y;
     }
-    const float2 q = __ldg(reinterpret_cast<const float2 *>(w + 4 * ws));
-    u[16] = q.x; u[17] = q.y;
   } else {
-    float t[24];
+    if (recon) {
+      float t[16];
+      unpack8<F16>(__ldg(w), t);
+      unpack8<F16>(__ldg(w + ws), t + 8);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) unpack8<F16>(__ldg(w + k * ws), t + 8 * k);
+      for (int k = 0; k < 12; ++k) u[k] = t[k];
+      reconstruct_row2<float>(u, t[12]);
+    } else {
+      float t[24];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) u[k] = t[k];
+      for (int k = 0; k < 3; ++k) unpack8<F16>(__ldg(w + k * ws), t + 8 * k);
+#pragma unroll
+      for (int k = 0; k < 18; ++k) u[k] = t[k];
+    }
   }
 }
 

@@ -50,24 +50,28 @@ struct F64 {
   static constexpr int kChunks = 12;
   static constexpr bool kHalf = false;
   static constexpr int kLinkChunks = 9;  // 18 doubles
+  static constexpr int kLinkChunksRecon = 9;  // never reconstructed
 };
 struct F32 {
   using R = float;
   static constexpr int kChunks = 6;
   static constexpr bool kHalf = false;
   static constexpr int kLinkChunks = 5;  // 18 floats + 2 pad
+  static constexpr int kLinkChunksRecon = 4;  // 12 floats + sign + 3 pad
 };
 struct F16 {
   using R = float;
   static constexpr int kChunks = 3;
   static constexpr bool kHalf = true;
   static constexpr int kLinkChunks = 3;  // 18 halves + 6 pad
+  static constexpr int kLinkChunksRecon = 2;  // 12 halves + sign + 3 pad
 };
 struct BF16 {
   using R = float;
   static constexpr int kChunks = 3;
   static constexpr bool kHalf = true;
   static constexpr int kLinkChunks = 3;  // links are stored as FP16
+  static constexpr int kLinkChunksRecon = 2;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -85,8 +89,13 @@ inline size_t field_rhs_bytes(dwf_prec p, size_t nsite, int Ls) {
   if (p == DWF_FP16 || p == DWF_BF16) d += align_up(nsite * Ls * sizeof(float), 256);
   return d;
 }
-inline size_t link_record_bytes(dwf_prec p) {
-  return p == DWF_FP64 ? 144 : (p == DWF_FP32 ? 80 : 48);
+// Bytes of one link record: 18 reals in 16-byte words (FP64 9, FP32 5, FP16 3);
+// with reconstruct-12 the first two rows, the boundary sign and padding
+// (FP32 4 words: 12 floats + sign; FP16 2 words: 12 halves + sign).
+inline size_t link_record_bytes(dwf_prec p, int recon = 0) {
+  if (p == DWF_FP64) return 144;
+  if (p == DWF_FP32) return recon ? 64 : 80;
+  return recon ? 32 : 48;
 }
 
 // A view of a native field: base of (block 0, rhs 0), byte strides.
@@ -129,6 +138,7 @@ struct HopParams {
   const char *links = nullptr;
   long long link_bstride = 0;
   int link_cs = 0;  // link owners per block: word k of (owner, mu) at (mu*words + k)*link_cs + owner
+  int recon = 0;       // 1: records hold two rows and a sign (reconstruct-12)
   const int *nbr = nullptr;  // [n_out][8], direction 2*mu + (0 fwd, 1 bwd)
   int n_out = 0;             // output sites per block
   int in_limit = 0;          // inputs with index >= in_limit are zero
@@ -266,9 +276,9 @@ void launch_import(dwf_prec p, char *native, long long nstride, const void *cano
 void launch_export(dwf_prec p, void *canon, int canon_fp32, const char *native,
                    long long nstride, int nsite, int Ls, const int dims[4], int nrhs,
                    cudaStream_t st);
-void launch_pack_links(const double *U, char *l64, char *l32, char *l16,
+void launch_pack_links(const double *U, char *l64, char *l32, char *l16, int recon,
                        const int dims[4], int t_antiperiodic, cudaStream_t st);
-void launch_block_links(dwf_prec p, char *dst, const char *src_l32, const char *src_l16,
+void launch_block_links(dwf_prec p, int recon, char *dst, const char *src_l32, const char *src_l16,
                         const int *gowner, int n_comb, int nblocks, const int dims[4],
                         cudaStream_t st);
 

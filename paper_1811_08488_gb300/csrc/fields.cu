@@ -166,8 +166,9 @@ void launch_export(dwf_prec p, void *canon, int canon_fp32, const char *native, 
 // antiperiodic sign.
 // ---------------------------------------------------------------------------
 __global__ void pack_links_kernel(const double *U, double *l64, float *l32, __half *l16, int Lx,
-                                  int Ly, int Lz, int Lt, int tap) {
+                                  int Ly, int Lz, int Lt, int tap, int recon) {
   const int V4 = Lx * Ly * Lz * Lt, Vh = V4 / 2;
+  const int w32 = recon ? 4 : 5, w16 = recon ? 2 : 3;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V4 * 4; i += gridDim.x * blockDim.x) {
     const int idx = i / 4, mu = i % 4;
     const int x = idx % Lx, y = (idx / Lx) % Ly, z = (idx / (Lx * Ly)) % Lz,
@@ -180,19 +181,25 @@ __global__ void pack_links_kernel(const double *U, double *l64, float *l32, __ha
     for (int k = 0; k < 24; ++k) v[k] = k < 18 ? sgn * src[k] : 0.0;
     for (int w = 0; w < 9; ++w)  // FP64: 2 reals per word
       for (int q = 0; q < 2; ++q) l64[(((size_t)mu * 9 + w) * V4 + owner) * 2 + q] = v[2 * w + q];
-    for (int w = 0; w < 5; ++w)  // FP32: 4 reals per word
+    if (recon) {
+      // the signed first two rows, then the sign: the third row is rebuilt
+      // on load as sign * conj(row0 x row1)
+      v[12] = sgn;
+      for (int k = 13; k < 24; ++k) v[k] = 0.0;
+    }
+    for (int w = 0; w < w32; ++w)  // FP32: 4 reals per word
       for (int q = 0; q < 4; ++q)
-        l32[(((size_t)mu * 5 + w) * V4 + owner) * 4 + q] = (float)v[4 * w + q];
-    for (int w = 0; w < 3; ++w)  // FP16: 8 reals per word
+        l32[(((size_t)mu * w32 + w) * V4 + owner) * 4 + q] = (float)v[4 * w + q];
+    for (int w = 0; w < w16; ++w)  // FP16: 8 reals per word
       for (int q = 0; q < 8; ++q)
-        l16[(((size_t)mu * 3 + w) * V4 + owner) * 8 + q] = __double2half(v[8 * w + q]);
+        l16[(((size_t)mu * w16 + w) * V4 + owner) * 8 + q] = __double2half(v[8 * w + q]);
   }
 }
 
-void launch_pack_links(const double *U, char *l64, char *l32, char *l16, const int dims[4],
-                       int tap, cudaStream_t st) {
+void launch_pack_links(const double *U, char *l64, char *l32, char *l16, int recon,
+                       const int dims[4], int tap, cudaStream_t st) {
   pack_links_kernel<<<1024, 256, 0, st>>>(U, (double *)l64, (float *)l32, (__half *)l16, dims[0],
-                                          dims[1], dims[2], dims[3], tap);
+                                          dims[1], dims[2], dims[3], tap, recon);
   DWF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -214,10 +221,10 @@ __global__ void block_links_kernel(char *dst, const char *src, int words, const 
   }
 }
 
-void launch_block_links(dwf_prec p, char *dst, const char *src_l32, const char *src_l16,
-                        const int *gowner, int n_comb, int nblocks, const int *dims,
-                        cudaStream_t st) {
-  const int rec = (int)link_record_bytes(p == DWF_FP32 ? DWF_FP32 : DWF_FP16);
+void launch_block_links(dwf_prec p, int recon, char *dst, const char *src_l32,
+                        const char *src_l16, const int *gowner, int n_comb, int nblocks,
+                        const int *dims, cudaStream_t st) {
+  const int rec = (int)link_record_bytes(p == DWF_FP32 ? DWF_FP32 : DWF_FP16, recon);
   const char *src = (p == DWF_FP32) ? src_l32 : src_l16;
   const int V4 = dims[0] * dims[1] * dims[2] * dims[3];
   block_links_kernel<<<1024, 256, 0, st>>>(dst, src, rec / 16, gowner, n_comb, nblocks, V4);

@@ -68,7 +68,7 @@ __device__ __forceinline__ void proj_mul_acc(R *acc, const R *v, const R *u);
 
 // One direction of the hop: project, multiply by U or U^+, reconstruct, add.
 // `lk` is the link record.
-template <class S, int MU, bool FWD, bool DAG, bool PRE>
+template <class S, int MU, bool FWD, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_dir(typename S::R *acc, const char *in, long long soff,
                                         int cs, int j, int s, int Ls, const uint4 *lk,
                                         size_t ls, const LsCoef &cf) {
@@ -91,7 +91,7 @@ __device__ __forceinline__ void hop_dir(typename S::R *acc, const char *in, long
     for (int k = 0; k < 12; ++k) v[12 + k] = b * v[12 + k] + c * fp * w[k];
   }
   R u[18];
-  load_link<S>(lk, ls, u);
+  load_link<S>(lk, ls, u, RC ? 1 : 0);
   proj_mul_acc<R, MU, FWD, DAG>(acc, v, u);
 }
 
@@ -144,19 +144,19 @@ __device__ __forceinline__ void proj_mul_acc(R *acc, const R *v, const R *u) {
   }
 }
 
-template <class S, int MU, bool DAG, bool PRE>
+template <class S, int MU, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_mu(typename S::R *acc, const HopParams &P, const char *in,
                                        const uint4 *links, const int *nb, int site, int s,
                                        const LsCoef &cf) {
-  constexpr int LC = S::kLinkChunks;
+  constexpr int LC = RC ? S::kLinkChunksRecon : S::kLinkChunks;
   const int jf = nb[2 * MU], jb = nb[2 * MU + 1];
   const size_t ls = (size_t)P.link_cs;
   const uint4 *lmu = links + (size_t)MU * LC * ls;
   if (jf >= 0 && jf < P.in_limit)
-    hop_dir<S, MU, true, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jf, s, P.Ls,
+    hop_dir<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, s, P.Ls,
                                    lmu + P.out_link_off + site, ls, cf);
   if (jb >= 0 && jb < P.in_limit)
-    hop_dir<S, MU, false, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jb, s, P.Ls,
+    hop_dir<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, s, P.Ls,
                                     lmu + P.in_link_off + jb, ls, cf);
 }
 
@@ -187,7 +187,7 @@ __device__ __forceinline__ void hop_dot(const HopParams &P, double d, double *re
 }
 
 // One thread per output (site, s): used for FP64 fields and odd Ls.
-template <class S, bool DAG, bool PRE>
+template <class S, bool DAG, bool PRE, bool RC>
 __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopParams P) {
   using R = typename S::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,10 +212,10 @@ __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopPar
   for (int k = 0; k < 24; ++k) acc[k] = 0;
   if (active) {
     const int *nb = P.nbr + (size_t)site * 8;
-    hop_mu<S, 0, DAG, PRE>(acc, P, in, links, nb, site, s, cf);
-    hop_mu<S, 1, DAG, PRE>(acc, P, in, links, nb, site, s, cf);
-    hop_mu<S, 2, DAG, PRE>(acc, P, in, links, nb, site, s, cf);
-    hop_mu<S, 3, DAG, PRE>(acc, P, in, links, nb, site, s, cf);
+    hop_mu<S, 0, DAG, PRE, RC>(acc, P, in, links, nb, site, s, cf);
+    hop_mu<S, 1, DAG, PRE, RC>(acc, P, in, links, nb, site, s, cf);
+    hop_mu<S, 2, DAG, PRE, RC>(acc, P, in, links, nb, site, s, cf);
+    hop_mu<S, 3, DAG, PRE, RC>(acc, P, in, links, nb, site, s, cf);
   }
   const int e = site * Ls + s;
 
@@ -308,9 +308,24 @@ template <> struct ProjAd<1> { static constexpr int s0 = 1, p0 = 0, s1 = 0, p1 =
 template <> struct ProjAd<2> { static constexpr int s0 = 0, p0 = 1, s1 = 1, p1 = 3; };
 template <> struct ProjAd<3> { static constexpr int s0 = 0, p0 = 0, s1 = 1, p1 = 0; };
 
+// x + y * s on both lanes (s = the two slices' scales, or their negatives).
+__device__ __forceinline__ float2 fma_s(float2 x, float2 y, float2 s) { return __ffma2_rn(y, s, x); }
+// x + sgn * sc * (ph * z): add_phase with the slices' scales folded in.
+template <int PH, int SGN>
+__device__ __forceinline__ C2 add_phase_s(C2 x, C2 z, float2 sp, float2 sn) {
+  const float2 a = SGN > 0 ? sp : sn, b = SGN > 0 ? sn : sp;  // +sgn*sc, -sgn*sc
+  if constexpr (PH == 0) return {fma_s(x.re, z.re, a), fma_s(x.im, z.im, a)};
+  else if constexpr (PH == 1) return {fma_s(x.re, z.im, b), fma_s(x.im, z.re, a)};
+  else if constexpr (PH == 2) return {fma_s(x.re, z.re, b), fma_s(x.im, z.im, b)};
+  else return {fma_s(x.re, z.im, a), fma_s(x.im, z.re, b)};
+}
+
 // Packed counterpart of proj_mul_acc: v, acc hold 24 reals of both slices.
-template <int MU, bool FWD, bool DAG>
-__device__ __forceinline__ void proj_mul_acc2(float2 *acc, const float2 *v, const float *u) {
+// SCALED: v holds stored FP16/BF16 values whose per-slice scales sc are
+// applied in the accumulation (the projector and U are linear).
+template <int MU, bool FWD, bool DAG, bool SCALED = false>
+__device__ __forceinline__ void proj_mul_acc2(float2 *acc, const float2 *v, const float *u,
+                                              float2 sc = make_float2(1.f, 1.f)) {
   constexpr int SG = (FWD != DAG) ? 1 : -1;  // projector (1 - SG g_mu)
   using A = ProjA<MU>;
   using Ad = ProjAd<MU>;
@@ -343,16 +358,30 @@ __device__ __forceinline__ void proj_mul_acc2(float2 *acc, const float2 *v, cons
       w[sp][a] = {re, im};
     }
   }
+  const float2 scn = make_float2(-sc.x, -sc.y);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    acc[0 * 6 + 2 * c] = __fadd2_rn(acc[0 * 6 + 2 * c], w[0][c].re);
-    acc[0 * 6 + 2 * c + 1] = __fadd2_rn(acc[0 * 6 + 2 * c + 1], w[0][c].im);
-    acc[1 * 6 + 2 * c] = __fadd2_rn(acc[1 * 6 + 2 * c], w[1][c].re);
-    acc[1 * 6 + 2 * c + 1] = __fadd2_rn(acc[1 * 6 + 2 * c + 1], w[1][c].im);
+    if constexpr (SCALED) {
+      acc[0 * 6 + 2 * c] = fma_s(acc[0 * 6 + 2 * c], w[0][c].re, sc);
+      acc[0 * 6 + 2 * c + 1] = fma_s(acc[0 * 6 + 2 * c + 1], w[0][c].im, sc);
+      acc[1 * 6 + 2 * c] = fma_s(acc[1 * 6 + 2 * c], w[1][c].re, sc);
+      acc[1 * 6 + 2 * c + 1] = fma_s(acc[1 * 6 + 2 * c + 1], w[1][c].im, sc);
+    } else {
+      acc[0 * 6 + 2 * c] = __fadd2_rn(acc[0 * 6 + 2 * c], w[0][c].re);
+      acc[0 * 6 + 2 * c + 1] = __fadd2_rn(acc[0 * 6 + 2 * c + 1], w[0][c].im);
+      acc[1 * 6 + 2 * c] = __fadd2_rn(acc[1 * 6 + 2 * c], w[1][c].re);
+      acc[1 * 6 + 2 * c + 1] = __fadd2_rn(acc[1 * 6 + 2 * c + 1], w[1][c].im);
+    }
     const C2 l0{acc[2 * 6 + 2 * c], acc[2 * 6 + 2 * c + 1]};
     const C2 l1{acc[3 * 6 + 2 * c], acc[3 * 6 + 2 * c + 1]};
-    const C2 n0 = add_phase<Ad::p0, -SG>(l0, w[Ad::s0][c]);
-    const C2 n1 = add_phase<Ad::p1, -SG>(l1, w[Ad::s1][c]);
+    C2 n0, n1;
+    if constexpr (SCALED) {
+      n0 = add_phase_s<Ad::p0, -SG>(l0, w[Ad::s0][c], sc, scn);
+      n1 = add_phase_s<Ad::p1, -SG>(l1, w[Ad::s1][c], sc, scn);
+    } else {
+      n0 = add_phase<Ad::p0, -SG>(l0, w[Ad::s0][c]);
+      n1 = add_phase<Ad::p1, -SG>(l1, w[Ad::s1][c]);
+    }
     acc[2 * 6 + 2 * c] = n0.re;
     acc[2 * 6 + 2 * c + 1] = n0.im;
     acc[3 * 6 + 2 * c] = n1.re;
@@ -360,12 +389,17 @@ __device__ __forceinline__ void proj_mul_acc2(float2 *acc, const float2 *v, cons
   }
 }
 
-template <class S, int MU, bool FWD, bool DAG, bool PRE>
+template <class S, int MU, bool FWD, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_dir2(float2 *acc, const char *in, long long soff, int cs,
                                          int j, int s0, int Ls, const uint4 *lk, size_t ls,
                                          const LsCoef &cf) {
   float v0[24], v1[24];
-  load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
+  constexpr bool kFold = !PRE && !std::is_same<S, F32>::value;  // scales folded into the FMAs
+  float2 sc = make_float2(1.f, 1.f);
+  if constexpr (kFold)
+    load24x2_unscaled<S>(in, soff, cs, j * Ls + s0, v0, v1, sc);
+  else
+    load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
   if constexpr (PRE) {
     const float b = cf.f.pre_b, c = cf.f.pre_c, mf = cf.f.mf;
     float w[12];
@@ -392,27 +426,27 @@ __device__ __forceinline__ void hop_dir2(float2 *acc, const char *in, long long 
 #pragma unroll
   for (int k = 0; k < 24; ++k) v[k] = make_float2(v0[k], v1[k]);
   float u[18];
-  load_link<S>(lk, ls, u);
-  proj_mul_acc2<MU, FWD, DAG>(acc, v, u);
+  load_link<S>(lk, ls, u, RC ? 1 : 0);
+  proj_mul_acc2<MU, FWD, DAG, kFold>(acc, v, u, sc);
 }
 
-template <class S, int MU, bool DAG, bool PRE>
+template <class S, int MU, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const char *in,
                                         const uint4 *links, const int *nb, int site, int s0,
                                         const LsCoef &cf) {
-  constexpr int LC = S::kLinkChunks;
+  constexpr int LC = RC ? S::kLinkChunksRecon : S::kLinkChunks;
   const int jf = nb[2 * MU], jb = nb[2 * MU + 1];
   const size_t ls = (size_t)P.link_cs;
   const uint4 *lmu = links + (size_t)MU * LC * ls;
   if (jf >= 0 && jf < P.in_limit)
-    hop_dir2<S, MU, true, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jf, s0, P.Ls,
+    hop_dir2<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, s0, P.Ls,
                                     lmu + P.out_link_off + site, ls, cf);
   if (jb >= 0 && jb < P.in_limit)
-    hop_dir2<S, MU, false, DAG, PRE>(acc, in, P.in.scale_off, P.in.cs, jb, s0, P.Ls,
+    hop_dir2<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, s0, P.Ls,
                                      lmu + P.in_link_off + jb, ls, cf);
 }
 
-template <class S, bool DAG, bool PRE>
+template <class S, bool DAG, bool PRE, bool RC>
 __global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ HopParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -437,10 +471,10 @@ __global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ Ho
   for (int k = 0; k < 24; ++k) acc[k] = make_float2(0.f, 0.f);
   if (active) {
     const int *nb = P.nbr + (size_t)site * 8;
-    hop_mu2<S, 0, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
-    hop_mu2<S, 1, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
-    hop_mu2<S, 2, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
-    hop_mu2<S, 3, DAG, PRE>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 0, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 1, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 2, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
+    hop_mu2<S, 3, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
   }
   const int e = site * Ls + s0;
   float a0[24], a1[24];
@@ -530,7 +564,7 @@ size_t hop_smem_bytes(int Ls, dwf_prec p, int epi, int has_x) {
   return (size_t)hop_sites_per_cta(Ls, p) * 24 * (Ls + 1) * rs * (has_x ? 2 : 1);
 }
 
-template <class S, bool DAG, bool PRE>
+template <class S, bool DAG, bool PRE, bool RC>
 static void launch_t(const HopParams &P0, int nrhs, cudaStream_t st, dwf_prec prec) {
   HopParams P = P0;
   for (int r = 0; r < nrhs; ++r) finalize_coef(P.coef[r]);
@@ -542,13 +576,13 @@ static void launch_t(const HopParams &P0, int nrhs, cudaStream_t st, dwf_prec pr
   if constexpr (!std::is_same<S, F64>::value) {
     if (hop_pairs(P.Ls, prec)) {
       dim3 block((nsites * (P.Ls / 2) + 31) / 32 * 32);
-      hop2_kernel<S, DAG, PRE><<<grid, block, smem, st>>>(P);
+      hop2_kernel<S, DAG, PRE, RC><<<grid, block, smem, st>>>(P);
       DWF_CUDA_TRY(cudaGetLastError());
       return;
     }
   }
   dim3 block((nsites * P.Ls + 31) / 32 * 32);
-  hop_kernel<S, DAG, PRE><<<grid, block, smem, st>>>(P);
+  hop_kernel<S, DAG, PRE, RC><<<grid, block, smem, st>>>(P);
   DWF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -562,12 +596,24 @@ template <class S>
 void launch_hop(const HopParams &P, int dagger, int pre_mphi, int nrhs, cudaStream_t st) {
   DWF_REQUIRE(!(dagger && pre_mphi), DWF_ERR_UNSUPPORTED, "M_phi on load is for Dhop only");
   const dwf_prec p = prec_of<S>();
+  if constexpr (!std::is_same<S, F64>::value) {
+    if (P.recon) {
+      if (dagger)
+        launch_t<S, true, false, true>(P, nrhs, st, p);
+      else if (pre_mphi)
+        launch_t<S, false, true, true>(P, nrhs, st, p);
+      else
+        launch_t<S, false, false, true>(P, nrhs, st, p);
+      return;
+    }
+  }
+  DWF_REQUIRE(!P.recon, DWF_ERR_UNSUPPORTED, "FP64 links are never reconstructed");
   if (dagger)
-    launch_t<S, true, false>(P, nrhs, st, p);
+    launch_t<S, true, false, false>(P, nrhs, st, p);
   else if (pre_mphi)
-    launch_t<S, false, true>(P, nrhs, st, p);
+    launch_t<S, false, true, false>(P, nrhs, st, p);
   else
-    launch_t<S, false, false>(P, nrhs, st, p);
+    launch_t<S, false, false, false>(P, nrhs, st, p);
 }
 
 // Allow the hop kernels more than 48 KB of dynamic shared memory. Called once
@@ -579,13 +625,19 @@ static void allow_big_smem(K *kernel) {
 }
 template <class S>
 static void prepare_one() {
-  allow_big_smem(hop_kernel<S, false, false>);
-  allow_big_smem(hop_kernel<S, false, true>);
-  allow_big_smem(hop_kernel<S, true, false>);
+  allow_big_smem(hop_kernel<S, false, false, false>);
+  allow_big_smem(hop_kernel<S, false, true, false>);
+  allow_big_smem(hop_kernel<S, true, false, false>);
   if constexpr (!std::is_same<S, F64>::value) {
-    allow_big_smem(hop2_kernel<S, false, false>);
-    allow_big_smem(hop2_kernel<S, false, true>);
-    allow_big_smem(hop2_kernel<S, true, false>);
+    allow_big_smem(hop_kernel<S, false, false, true>);
+    allow_big_smem(hop_kernel<S, false, true, true>);
+    allow_big_smem(hop_kernel<S, true, false, true>);
+    allow_big_smem(hop2_kernel<S, false, false, false>);
+    allow_big_smem(hop2_kernel<S, false, true, false>);
+    allow_big_smem(hop2_kernel<S, true, false, false>);
+    allow_big_smem(hop2_kernel<S, false, false, true>);
+    allow_big_smem(hop2_kernel<S, false, true, true>);
+    allow_big_smem(hop2_kernel<S, true, false, true>);
   }
 }
 void prepare_kernels() {

@@ -60,6 +60,7 @@ static HopParams global_params(const dwf_ctx *ctx, dwf_prec p, int out_parity, c
   P.out = global_ref(ctx, p, out);
   P.links = link_ptr(ctx, p);
   P.link_cs = ctx->geo.V4;
+  P.recon = (p != DWF_FP64 && ctx->act.recon12) ? 1 : 0;
   P.nbr = ctx->nbr_dev[out_parity].as<int>();
   P.n_out = ctx->geo.Vh;
   P.in_limit = ctx->geo.Vh;
@@ -203,9 +204,9 @@ BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int 
   const BlockGeometry &g = bp->bg;
   if (!bp->links_valid) {
     const dwf_prec lp = inner == DWF_FP32 ? DWF_FP32 : DWF_FP16;
-    bp->link_bstride = (long long)g.n_comb * 4 * (long long)link_record_bytes(lp);
+    bp->link_bstride = (long long)g.n_comb * 4 * (long long)link_record_bytes(lp, ctx->act.recon12);
     bp->links.ensure((size_t)bp->link_bstride * g.nblocks);
-    launch_block_links(lp, bp->links.c(), ctx->links[1].c(), ctx->links[2].c(),
+    launch_block_links(lp, ctx->act.recon12, bp->links.c(), ctx->links[1].c(), ctx->links[2].c(),
                        bp->gowner.as<int>(), g.n_comb, g.nblocks, ctx->act.dims, st);
     bp->links_valid = true;
   }
@@ -248,6 +249,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   base.links = bp->links.c();
   base.link_bstride = bp->link_bstride;
   base.link_cs = g.n_comb;
+  base.recon = ctx->act.recon12 ? 1 : 0;
   base.Ls = bp->Ls;
   base.nblocks = g.nblocks;
   base.skip = skip;

@@ -41,7 +41,7 @@ class DwfError(RuntimeError):
 
 class Action(C.Structure):
     _fields_ = [("dims", C.c_int * 4), ("Ls", C.c_int), ("b", C.c_double), ("c", C.c_double),
-                ("M5", C.c_double), ("t_antiperiodic", C.c_int)]
+                ("M5", C.c_double), ("t_antiperiodic", C.c_int), ("recon12", C.c_int)]
 
 
 class SolverParams(C.Structure):
@@ -138,7 +138,8 @@ def _masses(mf, nrhs=None):
 class Context:
     """A DWF context: lattice, action, packed links and work buffers."""
 
-    def __init__(self, dims, Ls, b=1.0, c=0.0, M5=1.8, t_antiperiodic=True, device=0):
+    def __init__(self, dims, Ls, b=1.0, c=0.0, M5=1.8, t_antiperiodic=True, device=0,
+                 recon12=False):
         self.dims = tuple(int(d) for d in dims)
         self.Ls = int(Ls)
         self.device = device
@@ -146,6 +147,7 @@ class Context:
         for i in range(4):
             a.dims[i] = self.dims[i]
         a.Ls, a.b, a.c, a.M5, a.t_antiperiodic = self.Ls, b, c, M5, int(bool(t_antiperiodic))
+        a.recon12 = int(bool(recon12))
         h = C.c_void_p()
         st = lib().dwf_create(C.byref(h), device, C.byref(a))
         if st != 0:

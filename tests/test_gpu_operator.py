@@ -36,11 +36,13 @@ def relerr(a, b):
 
 
 class Setup:
-    def __init__(self, dims, Ls, b=1.5, c=0.5, M5=1.8, eps=0.4, seed=1, antiperiodic=True):
+    def __init__(self, dims, Ls, b=1.5, c=0.5, M5=1.8, eps=0.4, seed=1, antiperiodic=True,
+                 recon12=False):
         self.act = op.Action(dims=tuple(dims), Ls=Ls, M5=M5, b=b, c=c, antiperiodic=antiperiodic)
         self.Uc = syn.gauge_field(dims, eps, seed)
         self.U = op.gauge_to_mu_major(self.Uc)
-        self.ctx = dwf().Context(dims, Ls, b=b, c=c, M5=M5, t_antiperiodic=antiperiodic)
+        self.ctx = dwf().Context(dims, Ls, b=b, c=c, M5=M5, t_antiperiodic=antiperiodic,
+                                 recon12=recon12)
         self.ctx.gauge_load(self.Uc)
 
     def to_native(self, halves, prec):
@@ -228,3 +230,70 @@ def test_dslash_full_size_sampled():
         want = pointwise.m4_at(S.act, S.Uc, src, (x, y, z, t), s, mf)
         g = got[s, t, z, y, x // 2]
         assert np.abs(g - want).max() < 1e-5 * np.abs(want).max()
+
+
+# ----------------------------------------------------------------------------
+# reconstruct-12 links: FP32/FP16 link records keep two rows and the boundary
+# sign; the operators must agree with the oracle at the same tolerances
+# (the third row is rebuilt from rows that are SU(3) to FP64 accuracy).
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,Ls,kw", [((4, 4, 4, 4), 4, dict()), ((4, 6, 2, 8), 5, dict(b=1.0, c=0.0)),
+                                        ((6, 4, 4, 2), 8, dict(antiperiodic=False))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_dslash_eo_recon12(dims, Ls, kw, prec, dagger):
+    S = Setup(dims, Ls, recon12=True, **kw)
+    masses = [0.03, 0.2]
+    ins = [S.source(13), S.source(14)]
+    for out_par in (0, 1):
+        nat_in = S.to_native(ins, prec)
+        nat_out = S.ctx.new_field(prec, 2)
+        S.ctx.dslash_eo(nat_out, nat_in, out_par, dagger, prec, masses)
+        got = S.from_native(nat_out, prec, 2)
+        for r in range(2):
+            full_in = op.half_to_full(ins[r], 1 - out_par)
+            want = op.full_to_half(op.m4(S.act, S.U, full_in, masses[r], bool(dagger)), out_par)
+            assert relerr(got[r], want) < TOL[prec], (out_par, r)
+
+
+def test_mdagm_and_block_apply_recon12():
+    S = Setup((8, 4, 6, 4), 4, recon12=True)
+    masses = [0.05, 0.3]
+    ins = [S.source(53), S.source(54)]
+    nat_in = S.to_native(ins, "fp32")
+    out = S.ctx.new_field("fp32", 2)
+    S.ctx.mdagm(out, nat_in, "fp32", masses)
+    got = S.from_native(out, "fp32", 2)
+    for r in range(2):
+        want = op.full_to_half(op.mdagm(S.act, S.U, op.half_to_full(ins[r], 0), masses[r]), 0)
+        assert relerr(got[r], want) < TOL["fp32"]
+    block = (2, 2, 2, 4)
+    for inner in ("fp32", "fp16"):
+        prm = dwf().default_params(block=block, inner=inner)
+        out = S.ctx.new_field("fp32", 2)
+        S.ctx.block_apply(out, nat_in, prm, masses)
+        got = S.from_native(out, "fp32", 2)
+        for r in range(2):
+            x = op.half_to_full(ins[r], 0)
+            want = np.zeros_like(x)
+            for o in sv.block_origins(S.act.dims, block):
+                m = sv.block_mask(S.act, block, o)
+                want += sv.a_block(S.act, S.U, sv.project(x, m), masses[r], m)
+            want = op.full_to_half(want, 0)
+            err = np.linalg.norm(got[r] - want) / np.linalg.norm(want)
+            assert err < BTOL[inner], (inner, r, err)
+
+
+def test_mspcg_solve_recon12():
+    S = Setup((4, 4, 4, 8), 6, recon12=True)
+    mf = 0.05
+    b = S.source(55)
+    bt = torch.from_numpy(b[None].copy()).cuda()
+    x = torch.zeros_like(bt)
+    prm = dwf().default_params(block=(2, 2, 2, 4), inner="fp16", inner_iters=4, tol=1e-10)
+    st, info = S.ctx.solve(x, bt, [mf], prm)
+    assert st == 0 and info[0]["converged"]
+    xf = op.half_to_full(x[0].cpu().numpy(), 0)
+    bf = op.half_to_full(b, 0)
+    r = bf - op.mdagm(S.act, S.U, xf, mf)
+    assert np.sqrt(op.norm2(r) / op.norm2(bf)) <= 1e-10
