@@ -317,6 +317,23 @@ def run_gpu(args, rank, world, dist):
     timed_solves(p_ms, args.warmup, False)
     with ClockSampler(dev) as clk:
         ms = timed_solves(p_ms, args.steps, True)
+    # the block autotuner's shape for this workload (the configured 8^3 x 16
+    # blocks stay the benchmark value): tuning cost and the solve with it
+    p_auto = dwf.default_params(inner_iters=6, block=(0, 0, 0, 0), inner="fp16", outer="fp32",
+                                tol=1e-10)
+    t0 = time.perf_counter()
+    blk_auto, _ = ctx.autotune_block(b, [mf], p_auto, trial=20)
+    t_tune = time.perf_counter() - t0
+    timed_solves(p_auto, 1, False)
+    auto = timed_solves(p_auto, max(1, args.steps // 2 + 1), True)
+    if dist:
+        auto_t = max_over_ranks([statistics.mean(t for t, _, _ in auto)], dist, "cuda")[0]
+    else:
+        auto_t = statistics.mean(t for t, _, _ in auto)
+    mspcg_auto = {"block": "x".join(map(str, blk_auto)), "seconds": round(auto_t, 6),
+                  "outer_iters": auto[-1][2]["outer_iters"], "tuning_seconds": round(t_tune, 3),
+                  "converged": all(st == 0 and i["converged"] for _, st, i in auto)}
+
     # e2e: host buffers, copies inside the timed region
     bh = torch.from_numpy(src[None].copy()).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
@@ -370,6 +387,7 @@ def run_gpu(args, rank, world, dist):
                      "reliable_updates": info_plain["reliable_updates"],
                      "true_resid": info_plain["true_resid"]},
         "mspcg_speedup_vs_plain": round(t_plain / t_ms, 4),
+        "mspcg_autotuned": mspcg_auto,
         "all_converged": ok,
         "dslash": {"kernel": "hop2_kernel<F32,DAG=0,PRE=1> (M^4 = -1/2 Dhop M_phi)",
                    "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
@@ -426,7 +444,7 @@ def run_study(args):
     w = syn.WORKLOADS[name]
     dims, Ls = w["dims"], w["Ls"]
     U, srcs = syn.workload_inputs(name)
-    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"])
+    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"], recon12=args.recon12)
     ctx.gauge_load(U)
     masses = list(w["mf"])
     stream = torch.cuda.current_stream()
@@ -435,6 +453,8 @@ def run_study(args):
     base = dict(block=w["block"], inner="fp16", outer="fp32", inner_iters=6, tol=1e-10)
     if args.maxiter:
         base["maxiter"] = args.maxiter
+    if args.delta:
+        base["delta"] = args.delta
 
     configs = []
     if args.study == "k":
@@ -503,7 +523,7 @@ def run_study(args):
                 infos += info
                 sts.append(st)
             outer = [i["outer_iters"] for i in infos]
-            line = {"study": args.study, "workload": name,
+            line = {"study": args.study, "workload": name, "recon12": bool(args.recon12),
                     "inner_iters": cfg["inner_iters"], "inner": cfg["inner"],
                     "block": "x".join(map(str, cfg["block"])), "snake": cfg.get("snake", 1),
                     "delta": cfg.get("delta", 0.1),
@@ -534,6 +554,8 @@ def main():
                     help="solver parameter sweep instead of the benchmark line")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
     ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")
+    ap.add_argument("--recon12", action="store_true", help="--study with reconstruct-12 links")
+    ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold of --study")
     args = ap.parse_args()
     if args.study:
         run_study(args)

@@ -147,7 +147,7 @@ const char *dwf_last_error(const dwf_ctx *ctx);
 
 /* Fill *p with the defaults: tol 1e-10, maxiter 100000, inner_iters 6,
  * block = {0,0,0,0} (must be set for MSPCG), outer FP32, inner FP16,
- * delta 0.1, snake 1, use_graph 1, io_on_host 0, check_every 10. */
+ * delta 0.001, snake 1, use_graph 1, io_on_host 0, check_every 10. */
 void dwf_solver_params_default(dwf_solver_params *p);
 
 /* Load the gauge field U (layout above; host pointer if on_device == 0).

@@ -108,7 +108,7 @@ void dwf_solver_params_default(dwf_solver_params *p) {
   p->inner_iters = 6;
   p->outer = DWF_FP32;
   p->inner = DWF_FP16;
-  p->delta = 0.1;
+  p->delta = 0.001;
   p->snake = 1;
   p->use_graph = 1;
   p->io_on_host = 0;

@@ -10,8 +10,9 @@
 // iterations from x = 0 on the caller's sources. With the largest true
 // residual res after n iterations, the rate is rho = res^(1/n) and the
 // predicted time to the tolerance is (t / n) * log(tol) / log(rho) (the time
-// itself when the trial already converged). The fastest prediction wins;
-// the other candidates' block plans are released.
+// itself when the trial already converged). The fastest prediction wins.
+// Each losing candidate's block plan is released as soon as it loses, and a
+// candidate whose plan does not fit in device memory is skipped.
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -88,50 +89,67 @@ void autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const double *mf,
   const bool debug = std::getenv("DWF_DEBUG") != nullptr;
   double best = std::numeric_limits<double>::infinity();
   std::array<int, 4> best_b = cands[0];
+  bool have_best = false;
+  // at most two candidates' block plans are held at a time: the best so far
+  // and the one on trial (a plan of small blocks on a large lattice holds
+  // tens of GB)
+  auto release = [&](const std::array<int, 4> &c) {
+    drop_graphs(ctx);
+    ctx->block_plans.erase(plan_key(c.data(), prm->inner));
+  };
   for (const auto &c : cands) {
     for (int i = 0; i < 4; ++i) p.block[i] = c[i];
-    p.maxiter = 1;
-    dwf_status s = solve(ctx, x, b, nrhs, mf, &p, info.data(), st);
-    if (s != DWF_OK && s != DWF_ERR_NOT_CONVERGED) continue;
-    p.maxiter = trial;
-    const auto t0 = std::chrono::steady_clock::now();
-    s = solve(ctx, x, b, nrhs, mf, &p, info.data(), st);
-    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (s != DWF_OK && s != DWF_ERR_NOT_CONVERGED) continue;
-    double pred = secs;
-    if (s == DWF_ERR_NOT_CONVERGED) {
-      double rho = 0.0;
-      int iters = 1;
-      for (int r = 0; r < nrhs; ++r) {
-        if (info[r].converged || info[r].outer_iters <= 0 || !(info[r].true_resid > 0)) continue;
-        const double rr = std::pow(info[r].true_resid, 1.0 / info[r].outer_iters);
-        if (rr > rho) {
-          rho = rr;
-          iters = info[r].outer_iters;
+    double pred = std::numeric_limits<double>::infinity();
+    double secs = 0.0;
+    try {
+      p.maxiter = 1;
+      dwf_status s = solve(ctx, x, b, nrhs, mf, &p, info.data(), st);
+      if (s == DWF_OK || s == DWF_ERR_NOT_CONVERGED) {
+        p.maxiter = trial;
+        const auto t0 = std::chrono::steady_clock::now();
+        s = solve(ctx, x, b, nrhs, mf, &p, info.data(), st);
+        secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (s == DWF_OK) {
+          pred = secs;
+        } else if (s == DWF_ERR_NOT_CONVERGED) {
+          double rho = 0.0;
+          int iters = 1;
+          for (int r = 0; r < nrhs; ++r) {
+            if (info[r].converged || info[r].outer_iters <= 0 || !(info[r].true_resid > 0))
+              continue;
+            const double rr = std::pow(info[r].true_resid, 1.0 / info[r].outer_iters);
+            if (rr > rho) {
+              rho = rr;
+              iters = info[r].outer_iters;
+            }
+          }
+          if (rho > 0.0 && rho < 1.0) pred = secs / iters * std::log(p.tol) / std::log(rho);
         }
       }
-      if (rho > 0.0 && rho < 1.0)
-        pred = secs / iters * std::log(p.tol) / std::log(rho);
-      else
-        pred = std::numeric_limits<double>::infinity();
+    } catch (const Error &e) {
+      // a candidate that does not fit in device memory is skipped
+      if (e.code != DWF_ERR_CUDA) throw;
+      cudaGetLastError();
+      DWF_CUDA_TRY(cudaStreamSynchronize(st));
+      if (debug)
+        std::fprintf(stderr, "[dwf] autotune %dx%dx%dx%d skipped: %s\n", c[0], c[1], c[2], c[3],
+                     e.msg.c_str());
     }
     if (debug)
       std::fprintf(stderr, "[dwf] autotune %dx%dx%dx%d: %.4f s for %d iterations, predicted %.4f s\n",
                    c[0], c[1], c[2], c[3], secs, trial, pred);
     if (pred < best) {
+      if (have_best) release(best_b);
       best = pred;
       best_b = c;
+      have_best = true;
+    } else {
+      release(c);
     }
   }
-  DWF_REQUIRE(std::isfinite(best), DWF_ERR_NOT_CONVERGED,
+  DWF_REQUIRE(have_best && std::isfinite(best), DWF_ERR_NOT_CONVERGED,
               "no candidate block shape reduced the residual in the trial");
-  // keep only the chosen plan of this inner precision
-  const std::string keep = plan_key(best_b.data(), prm->inner);
   drop_graphs(ctx);
-  for (const auto &c : cands) {
-    const std::string k = plan_key(c.data(), prm->inner);
-    if (k != keep) ctx->block_plans.erase(k);
-  }
   for (int i = 0; i < 4; ++i) block_out[i] = best_b[i];
   if (predicted) *predicted = best;
   ctx->tuned_blocks[tune_key(prm, nrhs, mf)] = best_b;

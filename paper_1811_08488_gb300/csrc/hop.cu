@@ -393,38 +393,40 @@ template <class S, int MU, bool FWD, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_dir2(float2 *acc, const char *in, long long soff, int cs,
                                          int j, int s0, int Ls, const uint4 *lk, size_t ls,
                                          const LsCoef &cf) {
-  float v0[24], v1[24];
+  float2 v[24];
   constexpr bool kFold = !PRE && !std::is_same<S, F32>::value;  // scales folded into the FMAs
   float2 sc = make_float2(1.f, 1.f);
-  if constexpr (kFold)
-    load24x2_unscaled<S>(in, soff, cs, j * Ls + s0, v0, v1, sc);
-  else
-    load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
-  if constexpr (PRE) {
-    const float b = cf.f.pre_b, c = cf.f.pre_c, mf = cf.f.mf;
-    float w[12];
-    const int sm = s0 == 0 ? Ls - 1 : s0 - 1;
-    const float fm = s0 == 0 ? -mf : 1.f;
-    load12<S, true>(in, soff, cs, j * Ls + sm, w);
+  {
+    float v0[24], v1[24];
+    if constexpr (kFold)
+      load24x2_unscaled<S>(in, soff, cs, j * Ls + s0, v0, v1, sc);
+    else
+      load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
+    if constexpr (PRE) {
+      // M_phi on both slices as packed FMAs: (chi(s0), chi(s0+1)) =
+      // b (v(s0), v(s0+1)) + c (shifted neighbours)
+      const float2 b2 = bc(cf.f.pre_b), c2 = bc(cf.f.pre_c);
+      const float mf = cf.f.mf;
+      float w[12];
+      const int sm = s0 == 0 ? Ls - 1 : s0 - 1;
+      const float fm = s0 == 0 ? -mf : 1.f;
+      load12<S, true>(in, soff, cs, j * Ls + sm, w);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {  // upper: chi(s0) <- s0-1, chi(s0+1) <- s0
-      const float t = v0[k];
-      v0[k] = b * t + c * fm * w[k];
-      v1[k] = b * v1[k] + c * t;
-    }
-    const int sp = s0 + 2 == Ls ? 0 : s0 + 2;
-    const float fp = s0 + 2 == Ls ? -mf : 1.f;
-    load12<S, false>(in, soff, cs, j * Ls + sp, w);
+      for (int k = 0; k < 12; ++k)  // upper: chi(s0) <- s0-1, chi(s0+1) <- s0
+        v[k] = __ffma2_rn(c2, make_float2(fm * w[k], v0[k]),
+                          __fmul2_rn(b2, make_float2(v0[k], v1[k])));
+      const int sp = s0 + 2 == Ls ? 0 : s0 + 2;
+      const float fp = s0 + 2 == Ls ? -mf : 1.f;
+      load12<S, false>(in, soff, cs, j * Ls + sp, w);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {  // lower: chi(s0) <- s0+1, chi(s0+1) <- s0+2
-      const float t = v1[12 + k];
-      v0[12 + k] = b * v0[12 + k] + c * t;
-      v1[12 + k] = b * t + c * fp * w[k];
+      for (int k = 0; k < 12; ++k)  // lower: chi(s0) <- s0+1, chi(s0+1) <- s0+2
+        v[12 + k] = __ffma2_rn(c2, make_float2(v1[12 + k], fp * w[k]),
+                               __fmul2_rn(b2, make_float2(v0[12 + k], v1[12 + k])));
+    } else {
+#pragma unroll
+      for (int k = 0; k < 24; ++k) v[k] = make_float2(v0[k], v1[k]);
     }
   }
-  float2 v[24];
-#pragma unroll
-  for (int k = 0; k < 24; ++k) v[k] = make_float2(v0[k], v1[k]);
   float u[18];
   load_link<S>(lk, ls, u, RC ? 1 : 0);
   proj_mul_acc2<MU, FWD, DAG, kFold>(acc, v, u, sc);
