@@ -34,9 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MSPCG vs plain CG time-to-solve at resid 1e-10 (1 GB300); Dslash HBM GB/s"
-# dram__bytes_read.sum + dram__bytes_write.sum of hop2_kernel<F32,0,1> on this
-# workload, one ncu capture (124.58 MB + 47.61 MB); see profiles/.
-HOP_FP32_DRAM_BYTES = 172192768
+# dram__bytes_read.sum + dram__bytes_write.sum of hop2_kernel<F32,0,1,0> on this
+# workload, one ncu capture (124.40 MB + 45.44 MB); see profiles/.
+HOP_FP32_DRAM_BYTES = 169840000
 WORKLOAD = "mobius_16^3x32x12"
 
 
@@ -400,7 +400,7 @@ def run_gpu(args, rank, world, dist):
         # `bench.py --dslash-only` (profiles/hop_fp32_mobius_16x16x16x32_Ls12.md)
         "roofline": {"bound": "hbm", "achieved": round(hop_gbs, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(hop_gbs / peak, 4), "traffic": HOP_FP32_DRAM_BYTES,
-                     "kernel": "hop2_kernel<F32,0,1>", "peak_kind": kind,
+                     "kernel": "hop2_kernel<F32,0,1,0>", "peak_kind": kind,
                      "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": round(t_e2e, 6), "unit": "s",
                 "h2d_bytes_per_step": int(bh.numel() * 16), "d2h_bytes_per_step": int(xh.numel() * 16)},

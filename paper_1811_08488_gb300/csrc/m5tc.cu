@@ -9,7 +9,9 @@
 // A CTA takes 32 sites of one right-hand side: 2 chiralities x 384 rows =
 // six M = 128 tiles; each tile is one tcgen05.mma of kind::f16 per K step of
 // 16 (Ls padded to LP = 16 or 32 with zero rows of B and zero columns of A),
-// accumulated in FP32 in tensor memory (TMEM).
+// accumulated in FP32 in tensor memory (TMEM). A is written in the MN-major
+// operand layout straight from coalesced global loads (the four rows of one
+// 16-byte input chunk are contiguous there), B (host-built) is K-major.
 //
 // Precision. Operands are FP16. Every (site, chirality) slab of A is first
 // scaled by a power of two so that its largest entry lies in [0.5, 1), and B
@@ -128,18 +130,6 @@ __host__ __device__ constexpr int tc_cols() {
   return kTcTiles * LP <= 128 ? 128 : 256;
 }
 
-// The A operands are written item by item: an item is 8 consecutive s (one
-// K group kg) of one 16-byte chunk c (4 reals r = 4(c % 3) .. +3 of chirality
-// c / 3) of one site h. The 3 KG items of a (site, chirality) slab sit in one
-// aligned group of G lanes, so the slab maximum is a G-lane shuffle reduction.
-template <int LP>
-struct TcShape {
-  static constexpr int KG = LP / 8;                        // K groups per row
-  static constexpr int G = (3 * KG <= 8) ? 8 : 16;         // lanes per slab
-  static constexpr int kSlabsPerRound = kTcThreads / G;    // slabs handled at once
-  static constexpr int kRounds = 2 * kTcSites / kSlabsPerRound;
-};
-
 // Bytes of the shared region that holds the A operands and, once the MMAs
 // are done, the FP32 output staging [chunk][site][s][4] (chunks padded by 16 B).
 template <int LP, bool SPLIT>
@@ -150,10 +140,26 @@ __host__ __device__ inline int tc_region_bytes(int Ls) {
   return (r + 127) / 128 * 128;
 }
 
+// Load the 4 reals 4c .. 4c+3 of element e (FP32 chunk c of the FP32 layout;
+// for FP16/BF16 the halves 4(c % 2) .. +3 of chunk c / 2, times the scale).
+template <class S>
+__device__ __forceinline__ float4 load_quad(const char *ip, long long soff, int cs, int c, int e) {
+  if constexpr (std::is_same<S, F32>::value) {
+    return __ldg(reinterpret_cast<const float4 *>(ip) + (size_t)c * cs + e);
+  } else {
+    const uint2 q = __ldg(reinterpret_cast<const uint2 *>(
+                              reinterpret_cast<const uint4 *>(ip) + (size_t)(c >> 1) * cs + e) +
+                          (c & 1));
+    float w[8];
+    unpack8<S>(make_uint4(q.x, q.y, 0u, 0u), w);
+    const float f = __ldg(reinterpret_cast<const float *>(ip + soff) + e);
+    return make_float4(w[0] * f, w[1] * f, w[2] * f, w[3] * f);
+  }
+}
+
 template <class S, int LP, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  using SH = TcShape<LP>;
   constexpr int kTileBytes = 128 * LP * 2;    // one M = 128 tile, K = LP FP16
   constexpr int kABytes = kTcTiles * kTileBytes;
   constexpr int kBImg = LP * LP * 2;          // one N x K image
@@ -164,8 +170,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
   unsigned char *A = smem;
   float *stg = reinterpret_cast<float *>(smem);
   unsigned char *B = smem + tc_region_bytes<LP, SPLIT>(Ls);
-  float *sig_inv = reinterpret_cast<float *>(B + 4 * kBImg);  // [site][chi]: 2^e
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(sig_inv + 2 * kTcSites);
+  float *sig = reinterpret_cast<float *>(B + 4 * kBImg);  // [site][chi]: 2^-e
+  float *sig_inv = sig + 2 * kTcSites;                      // 2^e
+  unsigned int *smax = reinterpret_cast<unsigned int *>(sig_inv + 2 * kTcSites);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smax + 2 * kTcSites);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -193,81 +201,65 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
     uint4 *dst = reinterpret_cast<uint4 *>(B);
     for (int i = tid; i < 4 * kBImg / 16; i += kTcThreads) dst[i] = __ldg(src + i);
   }
-
-  // A operands, canonical K-major layout without swizzle: row m of tile t,
-  // K group kg (8 FP16 = 16 bytes) at t*kTileBytes + (m/8)*(LP*16) + kg*128 + (m%8)*16.
-#pragma unroll 1
-  for (int round = 0; round < SH::kRounds; ++round) {
-    const int g = round * SH::kSlabsPerRound + tid / SH::G;  // slab = 2 h + chi
-    const int li = tid % SH::G;
-    const int h = g >> 1, chi = g & 1;
-    const bool item = li < 3 * SH::KG;
-    const int cc = item ? li / SH::KG : 0, kg = item ? li % SH::KG : 0;
-    const int c = chi * 3 + cc;
-    float4 v[8];
-    float m = 0.f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (item && h < nh) {
-      const int e0 = (h0 + h) * Ls + kg * 8;
-      if constexpr (std::is_same<S, F32>::value) {
-        const float4 *src = reinterpret_cast<const float4 *>(ip) + (size_t)c * cs + e0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (kg * 8 + q < Ls) v[q] = __ldg(src + q);
-      } else {
-        // FP16/BF16: reals 4c .. 4c+3 are halves 4(c % 2) .. +3 of chunk c / 2
-        const uint4 *src = reinterpret_cast<const uint4 *>(ip) + (size_t)(c >> 1) * cs + e0;
-        const float *scl = reinterpret_cast<const float *>(ip + P.soff) + e0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (kg * 8 + q < Ls) {
-            float w[8];
-            unpack8<S>(__ldg(src + q), w);
-            const float f = __ldg(scl + q);
-            const int o = (c & 1) * 4;
-            v[q] = make_float4(w[o] * f, w[o + 1] * f, w[o + 2] * f, w[o + 3] * f);
-          }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        m = fmaxf(m, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
-    }
-#pragma unroll
-    for (int o = 1; o < SH::G; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    // m = f 2^e with f in [0.5, 1): the scaled slab has its maximum in [0.5, 1)
-    const int ex = (m > 0.f && m < INFINITY) ? ((__float_as_int(m) >> 23) & 0xFF) - 126 : 0;
-    const float sc = pow2f(-ex);
-    if (li == 0) sig_inv[g] = pow2f(ex);
-    if (item) {
-      const int rho0 = h * 12 + 4 * cc;  // first row of the item within its chirality
-      const int t = chi * 3 + rho0 / 128, m0 = rho0 % 128;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float x[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 w = v[q];
-          x[q] = (j == 0 ? w.x : j == 1 ? w.y : j == 2 ? w.z : w.w) * sc;
-        }
-        uint4 hi, lo;
-        __half2 *ph = reinterpret_cast<__half2 *>(&hi), *pl = reinterpret_cast<__half2 *>(&lo);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const __half2 a = __floats2half2_rn(x[2 * q], x[2 * q + 1]);
-          ph[q] = a;
-          if (SPLIT) {
-            const float2 af = __half22float2(a);
-            pl[q] = __floats2half2_rn(x[2 * q] - af.x, x[2 * q + 1] - af.y);
-          }
-        }
-        const int mm = m0 + j;
-        const int off = t * kTileBytes + (mm >> 3) * (LP * 16) + kg * 128 + (mm & 7) * 16;
-        *reinterpret_cast<uint4 *>(A + off) = hi;
-        if (SPLIT) *reinterpret_cast<uint4 *>(A + kABytes + off) = lo;
-      }
-    }
+  if (tid < 2 * kTcSites) smax[tid] = 0u;
+  // A operands in the canonical MN-major layout without swizzle: element
+  // (row m, K index k) of tile t at t*kTileBytes + (m/8)*128 + (k/8)*2048 +
+  // (k%8)*16 + (m%8)*2, so the four consecutive rows of one 16-byte input
+  // chunk at one s are one 8-byte store. K indices s >= Ls are zero.
+  for (int i = tid; i < 2 * kTcTiles * 16 * (LP - Ls); i += kTcThreads) {
+    const int term = i / (kTcTiles * 16 * (LP - Ls)), r = i % (kTcTiles * 16 * (LP - Ls));
+    const int t = r / (16 * (LP - Ls)), g = (r / (LP - Ls)) % 16, k = Ls + r % (LP - Ls);
+    if (term == 0 || SPLIT)
+      *reinterpret_cast<uint4 *>(A + term * kABytes + t * kTileBytes + g * 128 + (k >> 3) * 2048 +
+                                 (k & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
   }
+  __syncthreads();
+  // slab maxima: non-negative floats order like their bit patterns
+  const int nq = 3 * kTcSites * Ls;  // quads of one chirality, all 32 site slots
+#pragma unroll 1
+  for (int chi = 0; chi < 2; ++chi)
+    for (int i = tid; i < nq; i += kTcThreads) {
+      const int cc = i / (kTcSites * Ls), e = i - cc * (kTcSites * Ls), h = e / Ls;
+      if (h >= nh) continue;
+      const float4 v = load_quad<S>(ip, P.soff, cs, chi * 3 + cc, h0 * Ls + e);
+      const float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+      atomicMax(smax + h * 2 + chi, __float_as_uint(m));
+    }
+  __syncthreads();
+  if (tid < 2 * kTcSites) {
+    // m = f 2^e with f in [0.5, 1): the scaled slab has its maximum in [0.5, 1)
+    const float m = __uint_as_float(smax[tid]);
+    const int ex = (m > 0.f && m < INFINITY) ? ((__float_as_int(m) >> 23) & 0xFF) - 126 : 0;
+    sig[tid] = pow2f(-ex);
+    sig_inv[tid] = pow2f(ex);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int chi = 0; chi < 2; ++chi)
+    for (int i = tid; i < nq; i += kTcThreads) {
+      const int cc = i / (kTcSites * Ls), e = i - cc * (kTcSites * Ls), h = e / Ls, k = e - h * Ls;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (h < nh) {
+        v = load_quad<S>(ip, P.soff, cs, chi * 3 + cc, h0 * Ls + e);
+        const float sc = sig[h * 2 + chi];
+        v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+      }
+      const __half2 a0 = __floats2half2_rn(v.x, v.y), a1 = __floats2half2_rn(v.z, v.w);
+      const int rho0 = h * 12 + 4 * cc;  // first of the four rows within the chirality
+      const int t = chi * 3 + rho0 / 128, m0 = rho0 % 128;
+      const int off = t * kTileBytes + (m0 >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (m0 & 7) * 2;
+      uint2 hi;
+      *reinterpret_cast<__half2 *>(&hi.x) = a0;
+      *reinterpret_cast<__half2 *>(&hi.y) = a1;
+      *reinterpret_cast<uint2 *>(A + off) = hi;
+      if (SPLIT) {
+        const float2 f0 = __half22float2(a0), f1 = __half22float2(a1);
+        uint2 lo;
+        *reinterpret_cast<__half2 *>(&lo.x) = __floats2half2_rn(v.x - f0.x, v.y - f0.y);
+        *reinterpret_cast<__half2 *>(&lo.y) = __floats2half2_rn(v.z - f1.x, v.w - f1.y);
+        *reinterpret_cast<uint2 *>(A + kABytes + off) = lo;
+      }
+    }
 
   // make the generic-proxy smem writes visible to the tensor core, then issue
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -276,8 +268,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
   if (tid == 0) {
-    // kind::f16, D FP32, A and B FP16, both K-major, N = LP, M = 128
-    const uint32_t idesc = (1u << 4) | ((uint32_t)(LP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // kind::f16, D FP32, A and B FP16, A MN-major, B K-major, N = LP, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 15) | ((uint32_t)(LP >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
     const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
     for (int t = 0; t < kTcTiles; ++t) {
       const int chi = t / 3;
@@ -286,7 +279,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
       for (int term = 0; term < (SPLIT ? 3 : 2); ++term) {
         const int at = term == 2 ? 1 : 0, bt = term == 1 ? 1 : 0;
         for (int kk = 0; kk < LP / 16; ++kk) {
-          const uint64_t ad = umma_desc(a0 + at * kABytes + t * kTileBytes + kk * 256, 128, LP * 16);
+          // A: K groups 2048 bytes apart (LBO), M groups 128 bytes apart (SBO)
+          const uint64_t ad = umma_desc(a0 + at * kABytes + t * kTileBytes + kk * 4096, 2048, 128);
           const uint64_t bd = umma_desc(b0 + (chi * 2 + bt) * kBImg + kk * 256, 128, LP * 16);
           umma_f16(tbase + t * LP, ad, bd, idesc, acc);
           acc = 1;
@@ -357,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
 template <int LP, bool SPLIT>
 size_t tc_smem_bytes(int Ls) {
   const size_t b = 4u * LP * LP * 2;
-  const size_t bytes = (size_t)tc_region_bytes<LP, SPLIT>(Ls) + b + 2u * kTcSites * 4 + 16;
+  const size_t bytes = (size_t)tc_region_bytes<LP, SPLIT>(Ls) + b + 3u * 2 * kTcSites * 4 + 16;
   // at least 48 KB: at most four CTAs (4 x 128 TMEM columns) share an SM
   return bytes < 48u * 1024 ? 48u * 1024 : bytes;
 }
