@@ -170,10 +170,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
   unsigned char *A = smem;
   float *stg = reinterpret_cast<float *>(smem);
   unsigned char *B = smem + tc_region_bytes<LP, SPLIT>(Ls);
-  float *sig = reinterpret_cast<float *>(B + 4 * kBImg);  // [site][chi]: 2^-e
-  float *sig_inv = sig + 2 * kTcSites;                      // 2^e
-  unsigned int *smax = reinterpret_cast<unsigned int *>(sig_inv + 2 * kTcSites);
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smax + 2 * kTcSites);
+  float *sig_inv = reinterpret_cast<float *>(B + 4 * kBImg);  // [site][chi]: 2^e
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sig_inv + 2 * kTcSites);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -201,7 +199,6 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
     uint4 *dst = reinterpret_cast<uint4 *>(B);
     for (int i = tid; i < 4 * kBImg / 16; i += kTcThreads) dst[i] = __ldg(src + i);
   }
-  if (tid < 2 * kTcSites) smax[tid] = 0u;
   // A operands in the canonical MN-major layout without swizzle: element
   // (row m, K index k) of tile t at t*kTileBytes + (m/8)*128 + (k/8)*2048 +
   // (k%8)*16 + (m%8)*2, so the four consecutive rows of one 16-byte input
@@ -213,53 +210,63 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
       *reinterpret_cast<uint4 *>(A + term * kABytes + t * kTileBytes + g * 128 + (k >> 3) * 2048 +
                                  (k & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
   }
-  __syncthreads();
-  // slab maxima: non-negative floats order like their bit patterns
-  const int nq = 3 * kTcSites * Ls;  // quads of one chirality, all 32 site slots
+  // Thread (site h = tid / 8, lane q = tid % 8) owns the quads of its site at
+  // s = q + 8j: the eight lanes of a site read its chunk rows as contiguous
+  // 128-byte pieces, and hold the whole (site, chirality) slab between them.
+  {
+    constexpr int KJ = LP / 8;  // s values per lane
+    const int h = tid >> 3, q = tid & 7;
+    const bool hv = h < nh;
 #pragma unroll 1
-  for (int chi = 0; chi < 2; ++chi)
-    for (int i = tid; i < nq; i += kTcThreads) {
-      const int cc = i / (kTcSites * Ls), e = i - cc * (kTcSites * Ls), h = e / Ls;
-      if (h >= nh) continue;
-      const float4 v = load_quad<S>(ip, P.soff, cs, chi * 3 + cc, h0 * Ls + e);
-      const float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-      atomicMax(smax + h * 2 + chi, __float_as_uint(m));
+    for (int chi = 0; chi < 2; ++chi) {
+      float m = 0.f;
+      float4 v[3][KJ];
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) {
+          const int k = q + 8 * j;
+          v[cc][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (hv && k < Ls) {
+            v[cc][j] = load_quad<S>(ip, P.soff, cs, chi * 3 + cc, (h0 + h) * Ls + k);
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v[cc][j].x), fabsf(v[cc][j].y)),
+                               fmaxf(fabsf(v[cc][j].z), fabsf(v[cc][j].w))));
+          }
+        }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      // m = f 2^e with f in [0.5, 1): the scaled slab has its maximum in [0.5, 1)
+      const int ex = (m > 0.f && m < INFINITY) ? ((__float_as_int(m) >> 23) & 0xFF) - 126 : 0;
+      const float sc = pow2f(-ex);
+      if (q == 0) sig_inv[h * 2 + chi] = pow2f(ex);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        const int rho0 = h * 12 + 4 * cc;  // first of the four rows within the chirality
+        const int t = chi * 3 + rho0 / 128, m0 = rho0 % 128;
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) {
+          const int k = q + 8 * j;
+          if (k >= Ls) continue;
+          const float4 w = make_float4(v[cc][j].x * sc, v[cc][j].y * sc, v[cc][j].z * sc,
+                                       v[cc][j].w * sc);
+          const __half2 a0 = __floats2half2_rn(w.x, w.y), a1 = __floats2half2_rn(w.z, w.w);
+          const int off = t * kTileBytes + (m0 >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 +
+                          (m0 & 7) * 2;
+          uint2 hi;
+          *reinterpret_cast<__half2 *>(&hi.x) = a0;
+          *reinterpret_cast<__half2 *>(&hi.y) = a1;
+          *reinterpret_cast<uint2 *>(A + off) = hi;
+          if (SPLIT) {
+            const float2 f0 = __half22float2(a0), f1 = __half22float2(a1);
+            uint2 lo;
+            *reinterpret_cast<__half2 *>(&lo.x) = __floats2half2_rn(w.x - f0.x, w.y - f0.y);
+            *reinterpret_cast<__half2 *>(&lo.y) = __floats2half2_rn(w.z - f1.x, w.w - f1.y);
+            *reinterpret_cast<uint2 *>(A + kABytes + off) = lo;
+          }
+        }
+      }
     }
-  __syncthreads();
-  if (tid < 2 * kTcSites) {
-    // m = f 2^e with f in [0.5, 1): the scaled slab has its maximum in [0.5, 1)
-    const float m = __uint_as_float(smax[tid]);
-    const int ex = (m > 0.f && m < INFINITY) ? ((__float_as_int(m) >> 23) & 0xFF) - 126 : 0;
-    sig[tid] = pow2f(-ex);
-    sig_inv[tid] = pow2f(ex);
   }
-  __syncthreads();
-#pragma unroll 1
-  for (int chi = 0; chi < 2; ++chi)
-    for (int i = tid; i < nq; i += kTcThreads) {
-      const int cc = i / (kTcSites * Ls), e = i - cc * (kTcSites * Ls), h = e / Ls, k = e - h * Ls;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (h < nh) {
-        v = load_quad<S>(ip, P.soff, cs, chi * 3 + cc, h0 * Ls + e);
-        const float sc = sig[h * 2 + chi];
-        v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
-      }
-      const __half2 a0 = __floats2half2_rn(v.x, v.y), a1 = __floats2half2_rn(v.z, v.w);
-      const int rho0 = h * 12 + 4 * cc;  // first of the four rows within the chirality
-      const int t = chi * 3 + rho0 / 128, m0 = rho0 % 128;
-      const int off = t * kTileBytes + (m0 >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (m0 & 7) * 2;
-      uint2 hi;
-      *reinterpret_cast<__half2 *>(&hi.x) = a0;
-      *reinterpret_cast<__half2 *>(&hi.y) = a1;
-      *reinterpret_cast<uint2 *>(A + off) = hi;
-      if (SPLIT) {
-        const float2 f0 = __half22float2(a0), f1 = __half22float2(a1);
-        uint2 lo;
-        *reinterpret_cast<__half2 *>(&lo.x) = __floats2half2_rn(v.x - f0.x, v.y - f0.y);
-        *reinterpret_cast<__half2 *>(&lo.y) = __floats2half2_rn(v.z - f1.x, v.w - f1.y);
-        *reinterpret_cast<uint2 *>(A + kABytes + off) = lo;
-      }
-    }
 
   // make the generic-proxy smem writes visible to the tensor core, then issue
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
 template <int LP, bool SPLIT>
 size_t tc_smem_bytes(int Ls) {
   const size_t b = 4u * LP * LP * 2;
-  const size_t bytes = (size_t)tc_region_bytes<LP, SPLIT>(Ls) + b + 3u * 2 * kTcSites * 4 + 16;
+  const size_t bytes = (size_t)tc_region_bytes<LP, SPLIT>(Ls) + b + 2u * kTcSites * 4 + 16;
   // at least 48 KB: at most four CTAs (4 x 128 TMEM columns) share an SM
   return bytes < 48u * 1024 ? 48u * 1024 : bytes;
 }
