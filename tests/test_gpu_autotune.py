@@ -60,3 +60,31 @@ def test_autotune_rejects_plain_cg():
     with pytest.raises(dwf.DwfError) as e:
         ctx.autotune_block(b, [MF], prm, trial=4)
     assert e.value.code == 1  # INVALID_ARG
+
+
+def test_autotune_without_candidates_is_unsupported():
+    """2^3 x 4 has no block of extent >= 4 in every direction: no candidate."""
+    from paper_1811_08488_gb300 import dwf
+    ctx = dwf.Context((2, 2, 2, 4), 4, b=1.5, c=0.5, M5=1.8)
+    ctx.gauge_load(syn.gauge_field((2, 2, 2, 4), 0.4, 3))
+    b = torch.from_numpy(syn.half_field((2, 2, 2, 4), 4, 4)[None].copy()).cuda()
+    prm = dwf.default_params(block=(0, 0, 0, 0), inner_iters=3)
+    with pytest.raises(dwf.DwfError) as e:
+        ctx.autotune_block(b, [MF], prm, trial=4)
+    assert e.value.code == 2  # UNSUPPORTED
+    with pytest.raises(dwf.DwfError) as e:
+        ctx.solve(torch.zeros_like(b), b, [MF], prm)
+    assert e.value.code == 2
+
+
+def test_autotune_with_host_buffers():
+    """io_on_host: the tuner's trial solves read b from host memory too."""
+    dwf, act, Uc, ctx, b = setup()
+    bh = b.cpu().numpy().copy()
+    prm = dwf.default_params(block=(0, 0, 0, 0), inner="fp16", inner_iters=4, tol=1e-10,
+                             io_on_host=1)
+    blk, pred = ctx.autotune_block(bh, [MF], prm, trial=4)
+    assert tuple(blk) in CANDIDATES and pred > 0
+    xh = np.zeros_like(bh)
+    st, info = ctx.solve(xh, bh, [MF], prm)
+    assert st == 0 and info[0]["converged"]
