@@ -108,3 +108,40 @@ def test_preconditioner_is_block_diagonal_at_full_size():
     # and on the block it is the same as with r everywhere
     diff = np.abs(np.where(inside, z_full - z_0, 0)).max()
     assert diff <= 1e-6 * np.abs(np.where(inside, z_full, 0)).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 3e-3)])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_m5inv_gemm_sixteen_rhs_full_size_sampled(prec, tol, dagger):
+    """The tensor-core M_5^-1 in the launch the benchmark times (16^3x32 x 12,
+    16 right-hand sides of log-spaced masses, one call) against the oracle's
+    dense inverse of M_5 on sampled (site, rhs) columns."""
+    name = "mobius_16^3x32x12_16rhs"
+    w = syn.WORKLOADS[name]
+    act = op.Action(dims=w["dims"], Ls=w["Ls"], M5=w["M5"], b=w["b"], c=w["c"])
+    ctx = dwf().Context(w["dims"], w["Ls"], b=w["b"], c=w["c"], M5=w["M5"])
+    _, srcs = syn.workload_inputs(name)
+    masses = list(w["mf"])
+    nr = len(masses)
+    canon = torch.from_numpy(np.ascontiguousarray(np.stack(srcs))).cuda()
+    fin, fout = ctx.new_field(prec, nr), ctx.new_field(prec, nr)
+    ctx.field_import(fin, prec, canon, nr)
+    ctx.m5inv_gemm(fout, fin, dagger, prec, masses)
+    got = torch.zeros_like(canon)
+    ctx.field_export(got, fout, prec, nr)
+    stored = torch.zeros_like(canon)
+    ctx.field_export(stored, fin, prec, nr)  # the input as stored (FP16 rounding included)
+    torch.cuda.synchronize()
+    got, stored = got.cpu().numpy(), stored.cpu().numpy()
+    rng = np.random.default_rng(7)
+    shape = got.shape[2:6]  # t, z, y, xh
+    err = scale = 0.0
+    for _ in range(32):
+        r = int(rng.integers(0, nr))
+        t, z, y, xh = (int(rng.integers(0, L)) for L in shape)
+        minv = np.linalg.inv(op.m5_matrix(act, masses[r], bool(dagger)))
+        col = stored[r, :, t, z, y, xh].reshape(w["Ls"] * 4, 3)
+        want = (minv @ col).reshape(w["Ls"], 4, 3)
+        err = max(err, np.abs(got[r, :, t, z, y, xh] - want).max())
+        scale = max(scale, np.abs(want).max())
+    assert err <= tol * scale, err / scale
