@@ -216,6 +216,26 @@ dwf_status dwf_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger,
 dwf_status dwf_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec,
                      int nrhs, const double *mf, void *stream);
 
+/* Right-hand side of the normal equation for the full system D psi = phi
+ * (paper eq. (dirac_equation) and eq. (normal_equation)):
+ *   phi_hat_e = phi_e - M^4_eo M_5^-1 phi_o,   b_even = D_PC^+ phi_hat_e.
+ * phi_even / phi_odd: the even and odd halves of phi; all three fields native
+ * (dwf_field_import) in prec, DWF_FP64 or DWF_FP32; b_even may not alias
+ * an input. Uses the context's operator temporaries. Errors: INVALID_ARG,
+ * NO_GAUGE, CUDA. */
+dwf_status dwf_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even,
+                           const void *phi_odd, dwf_prec prec, int nrhs,
+                           const double *mf, void *stream);
+
+/* The odd half of the solution of D psi = phi once the even half is known
+ * (the second row of the even-odd system, paper eq. (dirac_equation)):
+ *   psi_odd = M_5^-1 (phi_odd - M^4_oe psi_even).
+ * Native fields in prec (DWF_FP64 or DWF_FP32); psi_odd may not alias an
+ * input. Errors: INVALID_ARG, NO_GAUGE, CUDA. */
+dwf_status dwf_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
+                               const void *phi_odd, dwf_prec prec, int nrhs,
+                               const double *mf, void *stream);
+
 /* Size of the library's fixed device scratch array used by dwf_mdagm_noalloc. */
 #define DWF_NOALLOC_SCRATCH_BYTES (24u << 20)
 

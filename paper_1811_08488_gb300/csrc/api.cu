@@ -243,6 +243,37 @@ dwf_status dwf_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec, int
   API_CATCH(ctx)
 }
 
+dwf_status dwf_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even,
+                           const void *phi_odd, dwf_prec prec, int nrhs, const double *mf,
+                           void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(b_even && phi_even && phi_odd, DWF_ERR_INVALID_ARG, "null fields");
+  DWF_REQUIRE(b_even != phi_even && b_even != phi_odd, DWF_ERR_INVALID_ARG, "aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_source_prep(ctx, b_even, phi_even, phi_odd, prec, nrhs, mf, w,
+                         (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
+                               const void *phi_odd, dwf_prec prec, int nrhs, const double *mf,
+                               void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(psi_odd && psi_even && phi_odd, DWF_ERR_INVALID_ARG, "null fields");
+  DWF_REQUIRE(psi_odd != psi_even && psi_odd != phi_odd, DWF_ERR_INVALID_ARG,
+              "aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_odd_reconstruct(ctx, psi_odd, psi_even, phi_odd, prec, nrhs, mf, w,
+                             (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
 static void check_params(const dwf_solver_params *p) {
   DWF_REQUIRE(p != nullptr, DWF_ERR_INVALID_ARG, "null solver parameters");
 }

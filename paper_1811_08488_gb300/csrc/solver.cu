@@ -139,6 +139,56 @@ void apply_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, 
   mpc_second(ctx, out, odd, in, dagger, p, nrhs, mf, nullptr, nullptr, st);
 }
 
+// Right-hand side of the normal equation for the full system D psi = phi
+// (Sec. 2.2): phi_hat_e = phi_e - M^4_eo M_5^-1 phi_o, b = D_PC^+ phi_hat_e.
+// u = M_phi M_5^-1 phi_o (one Ls pass), then phi_hat_e = phi_e + 1/2 Dhop u
+// (the hop with phi_e added in its epilogue), then D_PC^+.
+void apply_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even, const void *phi_odd,
+                       dwf_prec p, int nrhs, const double *mf, const OpWork &w,
+                       cudaStream_t st) {
+  const int Vh = ctx->geo.Vh, Ls = ctx->act.Ls;
+  LsCoef c[kMaxRhs];
+  for (int r = 0; r < nrhs; ++r) c[r] = coef_k(ctx->act, mf[r], 1.0);
+  launch_ls_op(p, w.u, static_cast<const char *>(phi_odd), (long long)field_rhs_bytes(p, Vh, Ls),
+               Vh, Ls, 0, 1, nrhs, c, st);
+  HopParams P = global_params(ctx, p, 0, w.u, w.y);
+  P.xown = global_ref(ctx, p, phi_even);
+  for (int r = 0; r < nrhs; ++r) {
+    P.coef[r] = coef_identity(0.5);
+    P.coef[r].mf = mf[r];
+    P.coef[r].a0 = 1.0;
+    P.coef[r].a1 = 0.0;
+  }
+  P.epi = 1;
+  P.has_x = 1;
+  launch(p, P, 0, 0, nrhs, st);
+  apply_mpc(ctx, b_even, w.y, 1, p, nrhs, mf, w, st);
+}
+
+// The odd half of the solution of D psi = phi (Sec. 2.2):
+// psi_o = M_5^-1 (phi_o - M^4_oe psi_e) = M_5^-1 (phi_o + 1/2 Dhop M_phi psi_e).
+void apply_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
+                           const void *phi_odd, dwf_prec p, int nrhs, const double *mf,
+                           const OpWork &w, cudaStream_t st) {
+  const int Vh = ctx->geo.Vh, Ls = ctx->act.Ls;
+  HopParams P = global_params(ctx, p, 1, psi_even, w.u);
+  P.xown = global_ref(ctx, p, phi_odd);
+  for (int r = 0; r < nrhs; ++r) {
+    P.coef[r] = coef_identity(0.5);
+    P.coef[r].mf = mf[r];
+    with_pre(P.coef[r], ctx->act);
+    P.coef[r].a0 = 1.0;
+    P.coef[r].a1 = 0.0;
+  }
+  P.epi = 1;
+  P.has_x = 1;
+  launch(p, P, 0, 1, nrhs, st);
+  LsCoef c[kMaxRhs];
+  for (int r = 0; r < nrhs; ++r) c[r] = coef_m5inv(ctx->act, mf[r], 1.0);
+  launch_ls_op(p, static_cast<char *>(psi_odd), w.u, (long long)field_rhs_bytes(p, Vh, Ls), Vh,
+               Ls, 0, 1, nrhs, c, st);
+}
+
 void apply_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec p, int nrhs,
                  const double *mf, const OpWork &w, const DotSpec *dot, const int *skip,
                  cudaStream_t st) {

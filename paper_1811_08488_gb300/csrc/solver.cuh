@@ -29,6 +29,11 @@ void apply_dslash(dwf_ctx *ctx, void *out, const void *in, int out_parity, int d
                   dwf_prec p, int nrhs, const double *mf, cudaStream_t st);
 void apply_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
                const double *mf, const OpWork &w, cudaStream_t st);
+void apply_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even, const void *phi_odd,
+                       dwf_prec p, int nrhs, const double *mf, const OpWork &w, cudaStream_t st);
+void apply_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
+                           const void *phi_odd, dwf_prec p, int nrhs, const double *mf,
+                           const OpWork &w, cudaStream_t st);
 void apply_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec p, int nrhs,
                  const double *mf, const OpWork &w, const DotSpec *dot, const int *skip,
                  cudaStream_t st);

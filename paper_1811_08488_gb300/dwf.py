@@ -30,7 +30,8 @@ EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_def
            "dwf_gauge_load", "dwf_field_bytes", "dwf_field_import", "dwf_field_export",
            "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_m5inv_gemm", "dwf_mpc", "dwf_mdagm", "dwf_mdagm_noalloc",
            "dwf_block_apply",
-           "dwf_block_precond", "dwf_autotune_block", "mspcg_solve"]
+           "dwf_block_precond", "dwf_autotune_block", "dwf_source_prep", "dwf_odd_reconstruct",
+           "mspcg_solve"]
 
 
 class DwfError(RuntimeError):
@@ -82,6 +83,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_mpc": (I, [P, P, P, I, I, I, D, P]),
         "dwf_mdagm": (I, [P, P, P, I, I, D, P]),
         "dwf_mdagm_noalloc": (I, [P, P, P, I, I, D, P]),
+        "dwf_source_prep": (I, [P, P, P, P, I, I, D, P]),
+        "dwf_odd_reconstruct": (I, [P, P, P, P, I, I, D, P]),
         "dwf_block_apply": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "dwf_block_precond": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "mspcg_solve": (I, [P, P, P, I, D, C.POINTER(SolverParams), C.POINTER(SolveInfo), P]),
@@ -258,6 +261,43 @@ class Context:
                                             C.byref(params), m.size, mp, _stream(stream)))
 
     # ------------------------------------------------------------------- solve
+    def source_prep(self, b_even, phi_even, phi_odd, prec, mf, stream=None):
+        """dwf_source_prep: b = D_PC^+ (phi_e - M^4_eo M_5^-1 phi_o), native fields."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_source_prep(self._h, C.c_void_p(_ptr(b_even)),
+                                          C.c_void_p(_ptr(phi_even)), C.c_void_p(_ptr(phi_odd)),
+                                          PREC.get(prec, prec), m.size, mp, _stream(stream)))
+
+    def odd_reconstruct(self, psi_odd, psi_even, phi_odd, prec, mf, stream=None):
+        """dwf_odd_reconstruct: psi_o = M_5^-1 (phi_o - M^4_oe psi_e), native fields."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_odd_reconstruct(self._h, C.c_void_p(_ptr(psi_odd)),
+                                              C.c_void_p(_ptr(psi_even)),
+                                              C.c_void_p(_ptr(phi_odd)), PREC.get(prec, prec),
+                                              m.size, mp, _stream(stream)))
+
+    def solve_full(self, phi_even, phi_odd, mf, params, stream=None):
+        """Solve D psi = phi: source preparation, mspcg_solve on the normal
+        equation, odd reconstruction. phi_even / phi_odd: canonical complex128
+        device tensors [nrhs][...]; returns (psi_even, psi_odd, status, infos)
+        in the same layout. Every step runs in the library's kernels."""
+        import torch
+        m, _ = _masses(mf)
+        nrhs = m.size
+        nat = {k: self.new_field("fp64", nrhs) for k in ("pe", "po", "b", "xe", "xo")}
+        self.field_import(nat["pe"], "fp64", phi_even, nrhs)
+        self.field_import(nat["po"], "fp64", phi_odd, nrhs)
+        self.source_prep(nat["b"], nat["pe"], nat["po"], "fp64", list(m), stream)
+        b = torch.zeros_like(phi_even)
+        self.field_export(b, nat["b"], "fp64", nrhs)
+        psi_e = torch.zeros_like(phi_even)
+        st, info = self.solve(psi_e, b, list(m), params, stream)
+        self.field_import(nat["xe"], "fp64", psi_e, nrhs)
+        self.odd_reconstruct(nat["xo"], nat["xe"], nat["po"], "fp64", list(m), stream)
+        psi_o = torch.zeros_like(phi_odd)
+        self.field_export(psi_o, nat["xo"], "fp64", nrhs)
+        return psi_e, psi_o, st, info
+
     def autotune_block(self, b, mf, params, trial=20, stream=None):
         """dwf_autotune_block: returns (block shape, predicted seconds)."""
         m, mp = _masses(mf)

@@ -135,3 +135,55 @@ def test_error_codes():
     # zero source: x = 0, converged at once
     st, info, x = run(ctx, [np.zeros_like(src)], [0.01], inner_iters=2, block=(4, 4, 4, 4))
     assert st == 0 and info[0]["converged"] and np.all(x[0] == 0)
+
+
+# ----------------------------------------------------------------------------
+# the full system D psi = phi: source preparation, normal-equation solve, odd
+# reconstruction (the even-odd block system of Sec. 2.2)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_source_prep_and_odd_reconstruct(prec, tol):
+    act, Uc, U, ctx = setup((4, 4, 4, 8), 6, 1.5, 0.5, 0.4, 31)
+    masses = [0.05, 0.2]
+    pe = [syn.half_field(act.dims, act.Ls, 40 + r) for r in range(2)]
+    po = [syn.half_field(act.dims, act.Ls, 50 + r) for r in range(2)]
+    to = lambda hs: torch.from_numpy(np.ascontiguousarray(np.stack(hs))).cuda()
+    n_pe, n_po = ctx.new_field(prec, 2), ctx.new_field(prec, 2)
+    ctx.field_import(n_pe, prec, to(pe), 2)
+    ctx.field_import(n_po, prec, to(po), 2)
+    n_b = ctx.new_field(prec, 2)
+    ctx.source_prep(n_b, n_pe, n_po, prec, masses)
+    got = torch.zeros_like(to(pe))
+    ctx.field_export(got, n_b, prec, 2)
+    n_xo = ctx.new_field(prec, 2)
+    ctx.odd_reconstruct(n_xo, n_pe, n_po, prec, masses)  # psi_e := phi_e here
+    got_o = torch.zeros_like(to(po))
+    ctx.field_export(got_o, n_xo, prec, 2)
+    torch.cuda.synchronize()
+    got, got_o = got.cpu().numpy(), got_o.cpu().numpy()
+    for r in range(2):
+        fe, fo = op.half_to_full(pe[r], 0), op.half_to_full(po[r], 1)
+        phat = op.source_prep(act, U, fe, fo, masses[r])
+        want = op.full_to_half(op.mpc(act, U, phat, masses[r], True), 0)
+        assert np.abs(got[r] - want).max() <= tol * np.abs(want).max()
+        want_o = op.full_to_half(op.odd_reconstruct(act, U, fe, fo, masses[r]), 1)
+        assert np.abs(got_o[r] - want_o).max() <= tol * np.abs(want_o).max()
+
+
+def test_solve_full_system():
+    """psi from source_prep + MSPCG + odd_reconstruct solves D psi = phi
+    (D the oracle's unpreconditioned 5D operator)."""
+    act, Uc, U, ctx = setup((4, 4, 4, 8), 6, 1.5, 0.5, 0.4, 33)
+    mf = 0.05
+    phi_e = syn.half_field(act.dims, act.Ls, 60)
+    phi_o = syn.half_field(act.dims, act.Ls, 61)
+    te = torch.from_numpy(phi_e[None].copy()).cuda()
+    tof = torch.from_numpy(phi_o[None].copy()).cuda()
+    prm = dwf().default_params(block=(2, 2, 2, 4), inner="fp16", inner_iters=4, tol=1e-12,
+                               outer=dwf().DWF_FP64, maxiter=500)
+    psi_e, psi_o, st, info = ctx.solve_full(te, tof, [mf], prm)
+    assert st == 0 and info[0]["converged"]
+    psi = op.half_to_full(psi_e.cpu().numpy()[0], 0) + op.half_to_full(psi_o.cpu().numpy()[0], 1)
+    phi = op.half_to_full(phi_e, 0) + op.half_to_full(phi_o, 1)
+    r = phi - op.dwf_full(act, U, psi, mf)
+    assert np.sqrt(op.norm2(r) / op.norm2(phi)) < 1e-9
