@@ -517,6 +517,7 @@ def run_study(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3, st, info
 
+    default_delta = dwf.default_params().delta
     for cfg in configs:
         warm = dict(cfg, maxiter=2)
         if cfg.get("_batched", True):
@@ -535,7 +536,7 @@ def run_study(args):
             line = {"study": args.study, "workload": name, "recon12": bool(args.recon12),
                     "inner_iters": cfg["inner_iters"], "inner": cfg["inner"],
                     "block": "x".join(map(str, cfg["block"])), "snake": cfg.get("snake", 1),
-                    "delta": cfg.get("delta", 0.1),
+                    "delta": cfg.get("delta", default_delta),
                     "nrhs": len(masses), "one_call": cfg.get("_batched", True),
                     "seconds": round(t_tot, 4), "status": sts,
                     "outer_iters": outer, "max_outer_iters": max(outer),
