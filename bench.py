@@ -441,6 +441,7 @@ def run_study(args):
     pair   plain CG and MSPCG (k = 6) with the workload's block shape
     autotune  the block autotuner's pick, then the solve with block = 0
     delta  reliable-update threshold delta in {0.1, 0.03, 0.01, 0.001}, plain CG and k = 6
+    flexible  Algorithm 1's Fletcher-Reeves beta vs the flexible Polak-Ribiere beta (k = 6)
     Each configuration: one short untimed solve (plans, graphs), then
     `--steps` timed solves (CUDA events, L2 flushed before each). With
     `--maxiter` the solves stop after that many outer iterations and the
@@ -478,6 +479,8 @@ def run_study(args):
         configs = [dict(base, _batched=True), dict(base, _batched=False)]
     elif args.study == "pair":
         configs = [dict(base, inner_iters=0), dict(base)]
+    elif args.study == "flexible":
+        configs = [dict(base, flexible=f) for f in (0, 1)]
     elif args.study == "delta":
         configs = [dict(base, inner_iters=k, delta=d) for k in (0, 6) for d in (0.1, 0.03, 0.01, 0.001)]
     elif args.study == "autotune":
@@ -536,7 +539,7 @@ def run_study(args):
             line = {"study": args.study, "workload": name, "recon12": bool(args.recon12),
                     "inner_iters": cfg["inner_iters"], "inner": cfg["inner"],
                     "block": "x".join(map(str, cfg["block"])), "snake": cfg.get("snake", 1),
-                    "delta": cfg.get("delta", default_delta),
+                    "delta": cfg.get("delta", default_delta), "flexible": cfg.get("flexible", 0),
                     "nrhs": len(masses), "one_call": cfg.get("_batched", True),
                     "seconds": round(t_tot, 4), "status": sts,
                     "outer_iters": outer, "max_outer_iters": max(outer),
@@ -560,7 +563,8 @@ def main():
     ap.add_argument("--m5-only", action="store_true",
                     help="time only the tensor-core M_5^-1 (used for kernel profiles)")
     ap.add_argument("--m5-rhs", type=int, default=16, help="right-hand sides of the M_5^-1 timing")
-    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta"],
+    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta",
+                             "flexible"],
                     help="solver parameter sweep instead of the benchmark line")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
     ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")

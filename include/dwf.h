@@ -117,6 +117,9 @@ typedef struct {
   int use_graph;      /* 1: replay the iteration from a captured CUDA graph     */
   int io_on_host;     /* mspcg_solve: 1 = x and b are host pointers             */
   int check_every;    /* outer iterations between host convergence checks      */
+  int flexible;       /* 1: flexible PCG, beta = <r_new - r, z_new> / <r, z>    
+                       * (Polak-Ribiere); 0: Algorithm 1's <r_new, z_new> /   
+                       * <r, z> (Fletcher-Reeves)                             */
 } dwf_solver_params;
 
 /* Per right-hand-side result of mspcg_solve. */
@@ -147,7 +150,7 @@ const char *dwf_last_error(const dwf_ctx *ctx);
 
 /* Fill *p with the defaults: tol 1e-10, maxiter 100000, inner_iters 6,
  * block = {0,0,0,0} (must be set for MSPCG), outer FP32, inner FP16,
- * delta 0.001, snake 1, use_graph 1, io_on_host 0, check_every 10. */
+ * delta 0.001, snake 1, use_graph 1, io_on_host 0, check_every 10, flexible 0. */
 void dwf_solver_params_default(dwf_solver_params *p);
 
 /* Load the gauge field U (layout above; host pointer if on_device == 0).

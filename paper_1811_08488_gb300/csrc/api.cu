@@ -113,6 +113,7 @@ void dwf_solver_params_default(dwf_solver_params *p) {
   p->use_graph = 1;
   p->io_on_host = 0;
   p->check_every = 10;
+  p->flexible = 0;
 }
 
 dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device) {

@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(kBlasThreads) xpay_p_kernel(const OuterArgs A)
   OuterScalars *sc = A.scal + rhs;
   const double rzn = sc->rz_new;
   double beta_d;
-  const R beta = cta_ratio<R>(rzn, sc->rz, &beta_d);
+  // Fletcher-Reeves (Algorithm 1): <r', z'> / <r, z>; flexible (Polak-Ribiere):
+  // <r' - r, z'> / <r, z> = -alpha <A p, z'> / <r, z>
+  const R beta = cta_ratio<R>(A.flexible ? -sc->alpha * sc->apz : rzn, sc->rz, &beta_d);
   const long long o = rhs * A.rslo;
   const char *z = A.plain ? A.rlo : A.z;
   FLAT_LOOP(A.n4) {
@@ -291,7 +293,31 @@ int block_tiles(int n_b, int Ls) {
   return (int)(((long long)n_b * Ls + kBlasThreads - 1) / kBlasThreads);
 }
 
-template <class SI>
+// The global (outer) fields as floats: FP32 directly, FP64 converted.
+template <class G>
+__device__ __forceinline__ void load_glob(const char *base, int cs, int e, float *v) {
+  if constexpr (std::is_same<G, F32>::value) {
+    load24<F32>(base, 0, cs, e, v);
+  } else {
+    double t[24];
+    load24<F64>(base, 0, cs, e, t);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) v[k] = (float)t[k];
+  }
+}
+template <class G>
+__device__ __forceinline__ void store_glob(char *base, int cs, int e, const float *v) {
+  if constexpr (std::is_same<G, F32>::value) {
+    store24<F32>(base, 0, cs, e, v);
+  } else {
+    double t[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) t[k] = (double)v[k];
+    store24<F64>(base, 0, cs, e, t);
+  }
+}
+
+template <class SI, class G>
 __global__ void __launch_bounds__(kBlasThreads) blk_gather_kernel(const BlockArgs B) {
   __shared__ double red[32];
   const int rhs = blockIdx.z, b = blockIdx.y;
@@ -302,7 +328,7 @@ __global__ void __launch_bounds__(kBlasThreads) blk_gather_kernel(const BlockArg
   if (i < B.n_b) {
     const int h = B.gmap[(size_t)b * B.n_b + i];
     float v[24];
-    load24<F32>(B.rglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, v);
+    load_glob<G>(B.rglob + rhs * B.grs, B.gcs, h * B.Ls + s, v);
     float part = 0.f;
 #pragma unroll
     for (int k = 0; k < 24; ++k) part += v[k] * v[k];
@@ -395,30 +421,44 @@ __global__ void __launch_bounds__(kBlasThreads) blk_p_kernel(const BlockArgs B) 
 }
 
 // z_glob = x (block layout -> global), with <r, z> summed over all blocks.
+template <class G>
 __global__ void __launch_bounds__(kBlasThreads) blk_scatter_kernel(const BlockArgs B) {
   __shared__ double red[32];
   const int rhs = blockIdx.z, b = blockIdx.y;
   if (B.skip && B.skip[rhs]) return;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   if (i < B.n_b) {
     const int h = B.gmap[(size_t)b * B.n_b + i];
     float x[24], r[24];
     load24<F32>(B.x.data + rhs * B.x.rstride + b * B.x.bstride, 0, B.x.cs, i * B.Ls + s, x);
-    load24<F32>(B.rglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, r);
-    store24<F32>(B.zglob + rhs * B.grs, 0, B.gcs, h * B.Ls + s, x);
+    load_glob<G>(B.rglob + rhs * B.grs, B.gcs, h * B.Ls + s, r);
+    store_glob<G>(B.zglob + rhs * B.grs, B.gcs, h * B.Ls + s, x);
     float part = 0.f;
 #pragma unroll
     for (int k = 0; k < 24; ++k) part += r[k] * x[k];
     acc = part;
+    if (B.apglob) {
+      load_glob<G>(B.apglob + rhs * B.grs, B.gcs, h * B.Ls + s, r);
+      float part2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 24; ++k) part2 += r[k] * x[k];
+      acc2 = part2;
+    }
   }
   acc = cta_sum(acc, red);
   const int ntiles = gridDim.x * gridDim.y;
+  const int tile = b * gridDim.x + blockIdx.x;
   double tot;
-  if (group_reduce(acc, B.gpart + (size_t)rhs * ntiles, ntiles, b * gridDim.x + blockIdx.x,
-                   B.gcount + rhs, tot))
+  if (group_reduce(acc, B.gpart + (size_t)rhs * ntiles, ntiles, tile, B.gcount + rhs, tot))
     B.rz_out[(size_t)rhs * B.rz_rstride] = tot;
+  if (B.apglob) {
+    __syncthreads();
+    acc2 = cta_sum(acc2, red);
+    if (group_reduce(acc2, B.gpart2 + (size_t)rhs * ntiles, ntiles, tile, B.gcount2 + rhs, tot))
+      B.apz_out[(size_t)rhs * B.rz_rstride] = tot;
+  }
 }
 
 // out_glob = src (block layout -> FP32 global), used to read block vectors out.
@@ -462,7 +502,10 @@ void block_export(dwf_prec in, const BlockArgs &B, const FieldRef &src, int nrhs
 
 void block_gather(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st) {
   dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
-  DISPATCH_IN(in, blk_gather_kernel, );
+  if (B.gfp64)
+    DISPATCH_IN(in, blk_gather_kernel, , F64);
+  else
+    DISPATCH_IN(in, blk_gather_kernel, , F32);
 }
 void block_xr(dwf_prec in, const BlockArgs &B, int last, int nrhs, cudaStream_t st) {
   dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
@@ -477,7 +520,10 @@ void block_p(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st) {
 }
 void block_scatter(const BlockArgs &B, int nrhs, cudaStream_t st) {
   dim3 g(block_tiles(B.n_b, B.Ls), B.nblocks, nrhs);
-  blk_scatter_kernel<<<g, kBlasThreads, 0, st>>>(B);
+  if (B.gfp64)
+    blk_scatter_kernel<F64><<<g, kBlasThreads, 0, st>>>(B);
+  else
+    blk_scatter_kernel<F32><<<g, kBlasThreads, 0, st>>>(B);
   DWF_CUDA_TRY(cudaGetLastError());
 }
 

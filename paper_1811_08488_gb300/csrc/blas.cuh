@@ -20,14 +20,20 @@ struct OuterArgs {
   unsigned int *counters = nullptr;  // [rhs]
   const int *skip = nullptr;
   int plain = 0;                 // 1: z = r (no preconditioner)
+  int flexible = 0;              // 1: Polak-Ribiere beta = -alpha <Ap, z_new> / <r, z>
 };
 
 // Inner block CG (k iterations on every block at once).
 struct BlockArgs {
   FieldRef r, p, Ap;  // inner precision, block layout
   FieldRef x;         // FP32, block layout
-  const char *rglob = nullptr;  // FP32 native global even field
+  const char *rglob = nullptr;  // native global even field (FP32, or FP64 with gfp64)
   char *zglob = nullptr;
+  int gfp64 = 0;                // global fields are FP64 (FP64 outer solver)
+  const char *apglob = nullptr; // flexible PCG: global A p, for <A p, z>
+  double *apz_out = nullptr;    // apz_out[rhs * rz_rstride]
+  double *gpart2 = nullptr;     // second reduction of the scatter: [rhs][nblocks * tiles]
+  unsigned int *gcount2 = nullptr;
   long long grs = 0;            // global rhs stride
   int gcs = 0;                  // global elements per chunk plane: Vh * Ls
   const int *gmap = nullptr;    // [nblocks][n_b] global half index

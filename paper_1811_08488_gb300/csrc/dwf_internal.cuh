@@ -220,6 +220,7 @@ struct OuterScalars {
   double pAp;     // <p, A p>
   double rr;      // |r|^2 of the iterated residual
   double alpha, beta;
+  double apz;     // <A p, z_{k+1}> (flexible PCG)
   double bb;      // |b|^2
   int iter;       // iterations done
   int pad;

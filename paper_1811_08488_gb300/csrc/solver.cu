@@ -282,6 +282,9 @@ BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int 
     bp->gpart.ensure(sizeof(double) * (size_t)nrhs * nb * block_tiles(g.n_b, Ls));
     bp->gcount.ensure(sizeof(unsigned int) * nrhs);
     DWF_CUDA_TRY(cudaMemset(bp->gcount.p, 0, bp->gcount.bytes));
+    bp->gpart2.ensure(sizeof(double) * (size_t)nrhs * nb * block_tiles(g.n_b, Ls));
+    bp->gcount2.ensure(sizeof(unsigned int) * nrhs);
+    DWF_CUDA_TRY(cudaMemset(bp->gcount2.p, 0, bp->gcount2.bytes));
     bp->nrhs = nrhs;
   }
   return bp;
@@ -386,7 +389,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
 }
 
 BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double *rz_out,
-                            int rz_rstride, const int *skip) {
+                     int rz_rstride, const int *skip, dwf_prec glob) {
   const BlockGeometry &g = bp->bg;
   BlockArgs B;
   B.r = bp->fr;
@@ -395,7 +398,10 @@ BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double
   B.x = bp->fx;
   B.rglob = r;
   B.zglob = z;
-  B.grs = (long long)field_rhs_bytes(DWF_FP32, ctx->geo.Vh, ctx->act.Ls);
+  DWF_REQUIRE(glob == DWF_FP32 || glob == DWF_FP64, DWF_ERR_INVALID_ARG,
+              "the preconditioner takes FP32 or FP64 global fields");
+  B.gfp64 = glob == DWF_FP64 ? 1 : 0;
+  B.grs = (long long)field_rhs_bytes(glob, ctx->geo.Vh, ctx->act.Ls);
   B.gcs = ctx->geo.Vh * ctx->act.Ls;
   B.gmap = bp->gmap_b.as<int>();
   B.n_b = g.n_b;
@@ -410,6 +416,8 @@ BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double
   B.counters = bp->counters.as<unsigned int>();
   B.gpart = bp->gpart.as<double>();
   B.gcount = bp->gcount.as<unsigned int>();
+  B.gpart2 = bp->gpart2.as<double>();
+  B.gcount2 = bp->gcount2.as<unsigned int>();
   B.rz_out = rz_out ? rz_out : sc + 3 * n;  // scratch slot when unused
   B.rz_rstride = rz_out ? rz_rstride : 0;
   B.skip = skip;
@@ -420,8 +428,13 @@ BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double
 // block-local scalars from a zero guess, scatter the block solutions.
 void block_precondition(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, int k, int snake,
                         int nrhs, const double *mf, double *rz_out, int rz_rstride,
-                        const int *skip, cudaStream_t st) {
-  BlockArgs B = block_args(ctx, bp, z, r, rz_out, rz_rstride, skip);
+                        const int *skip, cudaStream_t st, dwf_prec glob, const char *ap,
+                        double *apz_out) {
+  BlockArgs B = block_args(ctx, bp, z, r, rz_out, rz_rstride, skip, glob);
+  if (ap && apz_out) {
+    B.apglob = ap;
+    B.apz_out = apz_out;
+  }
   block_gather(bp->inner, B, nrhs, st);
   for (int it = 0; it < k; ++it) {
     block_apply_A(ctx, bp, snake, nrhs, mf, true, skip, st);
@@ -513,7 +526,9 @@ static void enqueue_iteration(SolveSetup &S, cudaStream_t st) {
   if (!A.plain)
     block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
                        S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st);
+                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo,
+                       A.flexible ? sp->Ap.c() : nullptr,
+                       A.flexible ? &sp->scal.as<OuterScalars>()->apz : nullptr);
   outer_xpay_p(sp->lo, A, S.nrhs, st);
 }
 
@@ -530,7 +545,7 @@ static void enqueue_reliable_update(SolveSetup &S, cudaStream_t st) {
   if (!A.plain) {
     block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
                        S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st);
+                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo);
     outer_set_rz(A, S.nrhs, st);
   }
 }
@@ -567,6 +582,7 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   A.partials = sp->partials.as<double>();
   A.counters = sp->counters.as<unsigned int>();
   A.plain = plain ? 1 : 0;
+  A.flexible = (!plain && prm->flexible) ? 1 : 0;
   S.wlo = work_from(sp->wlo, lo, ctx, nrhs);
   S.w64 = work_from(sp->w64, DWF_FP64, ctx, nrhs);
   S.dot.partials = sp->opart.as<double>();
@@ -594,7 +610,7 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   if (!plain) {
     block_precondition(ctx, bp, sp->z.c(), sp->rlo.c(), prm->inner_iters, prm->snake, nrhs, mf,
                        &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), nullptr, st);
+                       (int)(sizeof(OuterScalars) / sizeof(double)), nullptr, st, lo);
     outer_set_rz(A, nrhs, st);
   }
   outer_copy_p(lo, A, nrhs, st);
@@ -603,7 +619,8 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   bool use_graph = prm->use_graph != 0 && st != nullptr;
   if (use_graph) {
     std::ostringstream key;
-    key << (void *)bp << "/" << (bp ? bp->r.p : nullptr) << "/" << prm->inner_iters << "/" << prm->snake << "/" << plain;
+    key << (void *)bp << "/" << (bp ? bp->r.p : nullptr) << "/" << prm->inner_iters << "/"
+        << prm->snake << "/" << plain << "/" << A.flexible;
     for (int r = 0; r < nrhs; ++r) key << "/" << mf[r];
     if (!sp->graph || sp->graph_key != key.str()) {
       if (sp->graph) cudaGraphExecDestroy(sp->graph);

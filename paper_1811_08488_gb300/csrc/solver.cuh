@@ -50,7 +50,7 @@ struct BlockPlan {
   DevBuf r, p, Ap, x, u1, y, u2;
   FieldRef fr, fp, fAp, fx, fu1, fy, fu2;
   DevBuf scal;  // rr, rr_new, pAp: 3 x [nrhs][nblocks] doubles
-  DevBuf partials, counters, gpart, gcount;
+  DevBuf partials, counters, gpart, gcount, gpart2, gcount2;
   bool links_valid = false;
 };
 
@@ -60,12 +60,15 @@ BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int 
 void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const double *mf,
                    bool with_dot, const int *skip, cudaStream_t st);
 // z = M^-1 r on FP32 global fields; <r, z> -> rz_out[rhs * rz_rstride] if given.
+// glob: precision of z and r (FP32, or FP64 for an FP64 outer solver). With
+// ap and apz_out, also <A p, z> -> apz_out[rhs * rz_rstride] (flexible PCG).
 void block_precondition(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, int k, int snake,
                         int nrhs, const double *mf, double *rz_out, int rz_rstride,
-                        const int *skip, cudaStream_t st);
+                        const int *skip, cudaStream_t st, dwf_prec glob = DWF_FP32,
+                        const char *ap = nullptr, double *apz_out = nullptr);
 
 BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double *rz_out,
-                     int rz_rstride, const int *skip);
+                     int rz_rstride, const int *skip, dwf_prec glob = DWF_FP32);
 
 struct SolverPlan {
   dwf_prec lo = DWF_FP32;

@@ -49,7 +49,7 @@ class SolverParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("inner_iters", C.c_int),
                 ("block", C.c_int * 4), ("outer", C.c_int), ("inner", C.c_int),
                 ("delta", C.c_double), ("snake", C.c_int), ("use_graph", C.c_int),
-                ("io_on_host", C.c_int), ("check_every", C.c_int)]
+                ("io_on_host", C.c_int), ("check_every", C.c_int), ("flexible", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -51,6 +51,7 @@ def test_binding_struct_layouts_match_header(libpath):
     assert p.tol == 1e-10 and p.maxiter == 100000 and p.inner_iters == 6
     assert p.outer == dwf.DWF_FP32 and p.inner == dwf.DWF_FP16
     assert p.delta == 0.001 and p.snake == 1 and p.use_graph == 1 and p.check_every == 10
+    assert p.flexible == 0
 
 
 def test_no_cpu_fallback_without_device(libpath):

@@ -187,3 +187,20 @@ def test_solve_full_system():
     phi = op.half_to_full(phi_e, 0) + op.half_to_full(phi_o, 1)
     r = phi - op.dwf_full(act, U, psi, mf)
     assert np.sqrt(op.norm2(r) / op.norm2(phi)) < 1e-9
+
+
+@pytest.mark.parametrize("flexible", [0, 1])
+@pytest.mark.parametrize("outer", ["fp32", "fp64"])
+def test_mspcg_flexible_and_fp64_outer(flexible, outer):
+    """MSPCG with the flexible (Polak-Ribiere) beta and with an FP64 outer
+    solver (the preconditioner then reads and writes FP64 global fields)."""
+    act, Uc, U, ctx = setup((4, 4, 4, 8), 6, 1.5, 0.5, 0.4, 35)
+    mf = 0.05
+    src = syn.half_field(act.dims, act.Ls, 70)
+    st, info, x = run(ctx, [src], [mf], inner_iters=4, block=(2, 2, 2, 4), inner="fp16",
+                      outer=dwf().PREC[outer], flexible=flexible, tol=1e-10, maxiter=2000)
+    assert st == 0 and info[0]["converged"]
+    assert oracle_resid(act, U, x[0], src, mf) <= 1e-10
+    # the preconditioner must work as one: far fewer iterations than plain CG
+    st0, info0, _ = run(ctx, [src], [mf], inner_iters=0, outer=dwf().PREC[outer], tol=1e-10)
+    assert info[0]["outer_iters"] < 0.7 * info0[0]["outer_iters"]
