@@ -324,9 +324,65 @@ __device__ __forceinline__ const LsK<R> &kc(const LsCoef &c) {
     return c.d;
 }
 
+// The column is first read into registers (LM >= Ls, loops unrolled over LM
+// with j < Ls guards, so no register array is indexed at run time) and the
+// recursions run there; shared memory is read once and written once.
+template <class R, int LM>
+__device__ __forceinline__ void ls_column_reg(R *T, const R *X, int Ls, bool down, bool inv,
+                                              const LsK<R> &c) {
+  auto ix = [&](int j) { return down ? j : Ls - 1 - j; };
+  const R mf = c.mf;
+  R v[LM];
+#pragma unroll
+  for (int j = 0; j < LM; ++j) v[j] = j < Ls ? T[ix(j)] : (R)0;
+  if (inv) {
+    // y_0 = (v_0 - mf sum_{j=1}^{Ls-1} r^(Ls-j) v_j) / (1 + mf r^Ls) by Horner,
+    // then y_j = v_j + r y_{j-1}
+    const R r = c.r;
+    R h = 0;
+#pragma unroll
+    for (int j = 1; j < LM; ++j)
+      if (j < Ls) h = h * r + v[j];
+    v[0] = (v[0] - mf * r * h) * c.inv_den;
+#pragma unroll
+    for (int j = 1; j < LM; ++j)
+      if (j < Ls) v[j] = v[j] + r * v[j - 1];
+  }
+  const R p0 = c.p0q, p1 = c.p1q;
+  R last = 0;
+#pragma unroll
+  for (int j = 0; j < LM; ++j)
+    if (j == Ls - 1) last = v[j];
+  R out_prev = v[0];
+  v[0] = p0 * v[0] - p1 * mf * last;
+#pragma unroll
+  for (int j = 1; j < LM; ++j)
+    if (j < Ls) {
+      const R t = v[j];
+      v[j] = p0 * t + p1 * out_prev;
+      out_prev = t;
+    }
+  if (X) {
+    const R a0 = c.a0, a1 = c.a1;
+    R xlast = X[ix(Ls - 1)], xprev = X[ix(0)];
+    v[0] += a0 * xprev - a1 * mf * xlast;
+#pragma unroll
+    for (int j = 1; j < LM; ++j)
+      if (j < Ls) {
+        const R xj = X[ix(j)];
+        v[j] += a0 * xj + a1 * xprev;
+        xprev = xj;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < LM; ++j)
+    if (j < Ls) T[ix(j)] = v[j];
+}
+
+// In-place walk over the shared-memory column.
 template <class R>
-__device__ __forceinline__ void ls_column(R *T, const R *X, int Ls, bool down, bool inv,
-                                          const LsK<R> &c) {
+__device__ __forceinline__ void ls_column_smem(R *T, const R *X, int Ls, bool down, bool inv,
+                                               const LsK<R> &c) {
   auto ix = [&](int j) { return down ? j : Ls - 1 - j; };
   const R mf = c.mf;
   if (inv) {
@@ -352,6 +408,16 @@ __device__ __forceinline__ void ls_column(R *T, const R *X, int Ls, bool down, b
     for (int j = 1; j < Ls; ++j) T[ix(j)] += a0 * X[ix(j)] + a1 * X[ix(j - 1)];
     T[ix(0)] += a0 * X[ix(0)] - a1 * mf * X[ix(Ls - 1)];
   }
+}
+
+// Columns of up to 16 slices run in registers, longer ones in place.
+template <class R>
+__device__ __forceinline__ void ls_column(R *T, const R *X, int Ls, bool down, bool inv,
+                                          const LsK<R> &c) {
+  if (Ls <= 16)
+    ls_column_reg<R, 16>(T, X, Ls, down, inv, c);
+  else
+    ls_column_smem<R>(T, X, Ls, down, inv, c);
 }
 
 // ---------------------------------------------------------------------------

@@ -448,7 +448,9 @@ __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const c
                                      lmu + P.in_link_off + jb, ls, cf);
 }
 
-template <class S, bool DAG, bool PRE, bool RC>
+// EPI: the Ls epilogue is compiled in (its column registers would otherwise
+// weigh on the plain hop's register allocation).
+template <class S, bool DAG, bool PRE, bool RC, bool EPI>
 __global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ HopParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ Ho
     a1[k] = acc[k].y;
   }
 
-  if (P.epi) {
+  if constexpr (EPI) {
     const int col = Ls + 1;
     float *T = reinterpret_cast<float *>(smem_raw);
     float *X = T + nsites * 24 * col;
@@ -578,7 +580,14 @@ static void launch_t(const HopParams &P0, int nrhs, cudaStream_t st, dwf_prec pr
   if constexpr (!std::is_same<S, F64>::value) {
     if (hop_pairs(P.Ls, prec)) {
       dim3 block((nsites * (P.Ls / 2) + 31) / 32 * 32);
-      hop2_kernel<S, DAG, PRE, RC><<<grid, block, smem, st>>>(P);
+      if (P.epi) {
+        hop2_kernel<S, DAG, PRE, RC, true><<<grid, block, smem, st>>>(P);
+      } else {
+        if constexpr (DAG)
+          throw Error{DWF_ERR_UNSUPPORTED, "the adjoint hop always has its M_phi^+ epilogue"};
+        else
+          hop2_kernel<S, DAG, PRE, RC, false><<<grid, block, smem, st>>>(P);
+      }
       DWF_CUDA_TRY(cudaGetLastError());
       return;
     }
@@ -634,12 +643,12 @@ static void prepare_one() {
     allow_big_smem(hop_kernel<S, false, false, true>);
     allow_big_smem(hop_kernel<S, false, true, true>);
     allow_big_smem(hop_kernel<S, true, false, true>);
-    allow_big_smem(hop2_kernel<S, false, false, false>);
-    allow_big_smem(hop2_kernel<S, false, true, false>);
-    allow_big_smem(hop2_kernel<S, true, false, false>);
-    allow_big_smem(hop2_kernel<S, false, false, true>);
-    allow_big_smem(hop2_kernel<S, false, true, true>);
-    allow_big_smem(hop2_kernel<S, true, false, true>);
+    allow_big_smem(hop2_kernel<S, false, false, false, true>);
+    allow_big_smem(hop2_kernel<S, false, true, false, true>);
+    allow_big_smem(hop2_kernel<S, true, false, false, true>);
+    allow_big_smem(hop2_kernel<S, false, false, true, true>);
+    allow_big_smem(hop2_kernel<S, false, true, true, true>);
+    allow_big_smem(hop2_kernel<S, true, false, true, true>);
   }
 }
 void prepare_kernels() {
