@@ -295,10 +295,17 @@ def run_gpu(args, rank, world, dist):
             times_dag.append(e0.elapsed_time(e1) * 1e-3)
         t_dag = statistics.median(times_dag)
         peak, kind = peaks()
-        return {"metric": "Dslash HBM GB/s", "value": round(hop_gbs, 1), "unit": "GB/s",
-                "higher_is_better": True, "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
-                "dagger_us": round(t_dag * 1e6, 2), "dagger_gbs": round(alg_bytes / t_dag / 1e9, 1),
-                "frac": round(hop_gbs / peak, 4), "config": {"workload": WORKLOAD}}, None, None
+        res = {"metric": "Dslash HBM GB/s", "value": round(hop_gbs, 1), "unit": "GB/s",
+               "higher_is_better": True, "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
+               "dagger_us": round(t_dag * 1e6, 2), "dagger_gbs": round(alg_bytes / t_dag / 1e9, 1),
+               "frac": round(hop_gbs / peak, 4), "config": {"workload": WORKLOAD}}
+        if args.dslash_fp64:
+            # the FP64 hop of the reliable updates (after the FP32 and FP16 launches)
+            d_in, d_out = ctx.new_field("fp64"), ctx.new_field("fp64")
+            ctx.field_import(d_in, "fp64", canon)
+            t64 = time_call(lambda: ctx.dslash_eo(d_out, d_in, 0, 0, "fp64", [mf]), 5)
+            res["fp64_us"] = round(t64 * 1e6, 1)
+        return res, None, None
 
     # --- solves -----------------------------------------------------------------
     b = canon
@@ -560,6 +567,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dslash-only", action="store_true",
                     help="time only the FP32 hop kernel (used for kernel profiles)")
+    ap.add_argument("--dslash-fp64", action="store_true",
+                    help="with --dslash-only: also time the FP64 hop")
     ap.add_argument("--m5-only", action="store_true",
                     help="time only the tensor-core M_5^-1 (used for kernel profiles)")
     ap.add_argument("--m5-rhs", type=int, default=16, help="right-hand sides of the M_5^-1 timing")
