@@ -616,7 +616,10 @@ def main():
         import torch
         import torch.distributed as td
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        td.init_process_group("nccl")
+        import datetime
+        # a replica that is lost between steps ends the others' next barrier
+        # or reduction with an error after this long instead of the default 10 min
+        td.init_process_group("nccl", timeout=datetime.timedelta(seconds=300))
         dist = td
     res, info_ms, nblocks = run_gpu(args, rank, world, dist)
     if rank == 0:

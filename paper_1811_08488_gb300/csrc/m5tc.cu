@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "device_common.cuh"
@@ -47,6 +48,8 @@ struct TcParams {
   float b_unscale[kMaxRhs][2];
   int nsite, Ls;
   int *status;        // set to 1 when a bounded wait gave up
+  int starve;                  // test hook: also wait for a phase nothing completes
+  unsigned long long wait_ns;  // limit of the bounded wait
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -299,7 +302,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
             smem_u32(mbar))
         : "memory");
   }
-  const bool ok = __syncthreads_and(mbar_wait_bounded(smem_u32(mbar), 0, 1000000000ull));
+  bool done = mbar_wait_bounded(smem_u32(mbar), 0, P.wait_ns);
+  // test hook: the second phase is never completed (no further arrival), so
+  // this wait runs out after the MMAs have finished (phase 0 above)
+  if (P.starve && done) done = mbar_wait_bounded(smem_u32(mbar), 1, P.wait_ns);
+  const bool ok = __syncthreads_and(done);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!ok && tid == 0) atomicExch(P.status, 1);
 
@@ -471,6 +478,18 @@ void launch_m5inv_gemm(dwf_ctx *ctx, dwf_prec p, char *out, const char *in, int 
   P.nsite = nsite;
   P.Ls = Ls;
   P.status = status;
+  P.starve = 0;
+  P.wait_ns = 1000000000ull;  // 1 s
+  // Failure-detection test hook: with DWF_TEST_STARVE_WAIT=1 every CTA, after
+  // its MMAs have completed, also waits for a barrier phase that nothing
+  // completes; the wait gives up after 1 ms, the CTA frees its TMEM and
+  // returns, and the call reports DWF_ERR_TIMEOUT.
+  if (const char *t = std::getenv("DWF_TEST_STARVE_WAIT")) {
+    if (t[0] == '1') {
+      P.starve = 1;
+      P.wait_ns = 1000000ull;
+    }
+  }
   dim3 grid((nsite + kTcSites - 1) / kTcSites, nrhs), block(kTcThreads);
 #define TCK(ST, L, SP)                                                                     \
   do {                                                                                     \

@@ -121,3 +121,22 @@ def test_m5inv_gemm_zero_field_and_errors():
     with pytest.raises(d.DwfError) as e:
         S.ctx.m5inv_gemm(o64, f64, 0, "fp64", [0.1])
     assert e.value.code == 2  # UNSUPPORTED
+
+
+def test_m5inv_gemm_bounded_wait_expires_and_context_survives(monkeypatch):
+    """Failure detection without a fault: DWF_TEST_STARVE_WAIT=1 makes every
+    CTA wait, after its MMAs, on a barrier phase nothing completes. The wait
+    gives up after 1 ms, the CTA frees its tensor memory and the call returns
+    DWF_ERR_TIMEOUT; the next call on the same context is exact again."""
+    S = Setup((4, 2, 2, 6), 12)
+    d = dwf()
+    src = S.source(5)
+    nat_in = S.to_native([src], "fp32")
+    out = S.ctx.new_field("fp32", 1)
+    monkeypatch.setenv("DWF_TEST_STARVE_WAIT", "1")
+    with pytest.raises(d.DwfError) as e:
+        S.ctx.m5inv_gemm(out, nat_in, 0, "fp32", [0.1])
+    assert e.value.code == 5  # TIMEOUT
+    monkeypatch.delenv("DWF_TEST_STARVE_WAIT")
+    S.ctx.m5inv_gemm(out, nat_in, 0, "fp32", [0.1])
+    assert relerr(S.from_native(out, "fp32", 1)[0], S.want(src, 0.1, 0)) < TOL["fp32"]

@@ -204,3 +204,22 @@ def test_mspcg_flexible_and_fp64_outer(flexible, outer):
     # the preconditioner must work as one: far fewer iterations than plain CG
     st0, info0, _ = run(ctx, [src], [mf], inner_iters=0, outer=dwf().PREC[outer], tol=1e-10)
     assert info[0]["outer_iters"] < 0.7 * info0[0]["outer_iters"]
+
+
+def test_nan_source_reports_nan_and_context_survives():
+    """A NaN in b reaches the outer residual; the host sees a non-finite |r|^2
+    at its first check and returns DWF_ERR_NAN. The same context then solves a
+    finite system to the tolerance."""
+    act, Uc, U, ctx = setup((4, 4, 4, 8), 8, 1.5, 0.5, 0.3, 1010)
+    bad = syn.half_field(act.dims, act.Ls, 2010)
+    bad.flat[17] = np.nan
+    b = torch.from_numpy(bad[None].copy()).cuda()
+    x = torch.zeros_like(b)
+    prm = dwf().default_params(block=(4, 4, 4, 4), inner_iters=4, tol=1e-10)
+    st, info = ctx.solve(x, b, [0.1], prm, raise_on_error=False)
+    assert st == 6  # NAN
+    assert not info[0]["converged"]
+    src = syn.half_field(act.dims, act.Ls, 2011)
+    st, info, xs = run(ctx, [src], [0.1], block=(4, 4, 4, 4), inner_iters=4, tol=1e-10)
+    assert st == 0 and info[0]["converged"]
+    assert oracle_resid(act, U, xs[0], src, 0.1) <= 1e-10
