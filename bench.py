@@ -437,6 +437,50 @@ STUDY_BLOCKS = [(4, 4, 4, 4), (6, 6, 6, 8), (8, 8, 8, 8), (8, 8, 8, 16), (12, 12
                 (12, 12, 12, 16), (16, 16, 16, 16)]
 
 
+def run_resident_study(args):
+    """Per-block cost of the block preconditioner against the number of blocks.
+
+    With 2 or 4 blocks of 8^3 x 16 (Ls = 12, FP16 inner storage) the whole
+    working set of the k inner iterations stays in the 129 MB L2; with 16 or
+    32 it streams from HBM. Equal per-block times mean that keeping blocks
+    resident in L2 would not pay."""
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    block, Ls, k = (8, 8, 8, 16), 12, 6
+    for dims in [(16, 8, 8, 16), (16, 16, 8, 16), (16, 16, 16, 16), (16, 16, 16, 32),
+                 (32, 16, 16, 32)]:
+        ctx = dwf.Context(dims, Ls, b=1.5, c=0.5, M5=1.8)
+        ctx.gauge_load(syn.gauge_field(dims, 0.4, 1002))
+        canon = torch.from_numpy(syn.half_field(dims, Ls, 2002)[None].copy()).cuda()
+        r, z = ctx.new_field("fp32", 1), ctx.new_field("fp32", 1)
+        ctx.field_import(r, "fp32", canon, 1)
+        prm = dwf.default_params(block=block, inner="fp16", inner_iters=k)
+        for _ in range(3):
+            ctx.block_precond(z, r, prm, [0.01])
+        res = {}
+        for mode in ("warm", "flushed"):
+            ts = []
+            for _ in range(max(args.steps, 5)):
+                if mode == "flushed":
+                    flush_l2(flush)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.block_precond(z, r, prm, [0.01])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3)
+            res[mode] = float(np.median(ts))
+        nb = int(np.prod([d // b for d, b in zip(dims, block)]))
+        print(json.dumps({"study": "resident", "dims": "x".join(map(str, dims)), "Ls": Ls,
+                          "block": "x".join(map(str, block)), "blocks": nb, "inner_iters": k,
+                          "inner": "fp16", "us": {m: round(v, 1) for m, v in res.items()},
+                          "us_per_block": {m: round(v / nb, 1) for m, v in res.items()}}),
+              flush=True)
+        del ctx
+
+
 def run_study(args):
     """Time MSPCG / plain CG solves of one workload over a parameter sweep.
 
@@ -447,6 +491,9 @@ def run_study(args):
     rhs    all right-hand sides of the workload in one call vs one call each
     pair   plain CG and MSPCG (k = 6) with the workload's block shape
     autotune  the block autotuner's pick, then the solve with block = 0
+    resident  the k = 6 block preconditioner alone, per 8^3 x 16 block, on
+           lattices of 2 to 32 such blocks (working set from well inside L2
+           to several times L2), timed warm and with L2 flushed
     delta  reliable-update threshold delta in {0.1, 0.03, 0.01, 0.001}, plain CG and k = 6
     flexible  Algorithm 1's Fletcher-Reeves beta vs the flexible Polak-Ribiere beta (k = 6)
     Each configuration: one short untimed solve (plans, graphs), then
@@ -457,6 +504,9 @@ def run_study(args):
     import torch
     from paper_1811_08488_gb300 import dwf, synthetic as syn
     torch.cuda.set_device(0)
+    if args.study == "resident":
+        run_resident_study(args)
+        return
     name = args.workload
     w = syn.WORKLOADS[name]
     dims, Ls = w["dims"], w["Ls"]
@@ -572,7 +622,7 @@ def main():
     ap.add_argument("--m5-only", action="store_true",
                     help="time only the tensor-core M_5^-1 (used for kernel profiles)")
     ap.add_argument("--m5-rhs", type=int, default=16, help="right-hand sides of the M_5^-1 timing")
-    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta",
+    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta", "resident",
                              "flexible"],
                     help="solver parameter sweep instead of the benchmark line")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
