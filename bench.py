@@ -35,9 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MSPCG vs plain CG time-to-solve at resid 1e-10 (1 GB300); Dslash HBM GB/s"
-# dram__bytes_read.sum + dram__bytes_write.sum of hop2_kernel<F32,0,1,0> on this
-# workload, one ncu capture (124.40 MB + 45.44 MB); see profiles/.
-HOP_FP32_DRAM_BYTES = 169840000
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the hop kernels
+# inside the MSPCG solve of this workload, from one ncu capture of the same
+# bench command on the current kernels (see profiles/); a kernel missing here
+# reports traffic null.
+DRAM_BYTES_PER_LAUNCH = {}
 WORKLOAD = "mobius_16^3x32x12"
 
 
@@ -334,9 +336,19 @@ def run_gpu(args, rank, world, dist):
 
     timed_solves(p_plain, max(1, args.warmup // 2), False)
     plain = timed_solves(p_plain, max(1, args.steps // 2 + 1), True)
+    # the hop-kernel timer runs inside the timed MSPCG solves: its graphs are
+    # captured with the timer during the warm-up, and the counters are reset
+    # right before the timed region
+    ctx.profile(True)
     timed_solves(p_ms, args.warmup, False)
+    ctx.profile(True)
     with ClockSampler(dev) as clk:
         ms = timed_solves(p_ms, args.steps, True)
+    kstats = ctx.profile_read()
+    ctx.profile(False)
+    # the same solves without the timer (its cost, for the record)
+    timed_solves(p_ms, 1, False)
+    ms_off = timed_solves(p_ms, max(1, args.steps // 2 + 1), True)
     # the block autotuner's shape for this workload (the configured 8^3 x 16
     # blocks stay the benchmark value): tuning cost and the solve with it
     p_auto = dwf.default_params(inner_iters=6, block=(0, 0, 0, 0), inner="fp16", outer="fp32",
@@ -381,6 +393,19 @@ def run_gpu(args, rank, world, dist):
     launches_ms = (1 + 1 + (6 * k + 1) + 2 + info_ms["outer_iters"] * (6 + 6 * k + 1)
                    + info_ms["reliable_updates"] * (6 + 6 * k + 2) + 1)
     peak, kind = peaks()
+    # the dominant kernel of the timed solves, from the hop-kernel timer:
+    # achieved = its compulsory bytes / its device time, summed over launches
+    t_steps = sum(t for t, _, _ in ms)
+    kernels = []
+    for kst in sorted(kstats, key=lambda d: -d["seconds"]):
+        kernels.append({"kernel": kst["name"], "launches": kst["launches"],
+                        "ms": round(kst["seconds"] * 1e3, 3),
+                        "share": round(kst["seconds"] / t_steps, 4),
+                        "avg_us": round(kst["seconds"] / kst["launches"] * 1e6, 2),
+                        "gbs": round(kst["alg_bytes"] / kst["seconds"] / 1e9, 1)})
+    dom = max(kstats, key=lambda d: d["seconds"])
+    dom_gbs = dom["alg_bytes"] / dom["seconds"] / 1e9
+    dom_traffic = DRAM_BYTES_PER_LAUNCH.get(dom["name"])
     res = {
         "metric": METRIC,
         "value": round(t_ms, 6),
@@ -395,7 +420,9 @@ def run_gpu(args, rank, world, dist):
         "dtype": "f32",
         "data": "synthetic",
         "config": bench_config(world),
-        "mspcg": {"seconds": round(t_ms, 6), "outer_iters": info_ms["outer_iters"],
+        "mspcg": {"seconds": round(t_ms, 6),
+                  "seconds_without_kernel_timer": round(statistics.mean(t for t, _, _ in ms_off), 6),
+                  "outer_iters": info_ms["outer_iters"],
                   "inner_iters_total": info_ms["inner_iters_total"],
                   "reliable_updates": info_ms["reliable_updates"],
                   "true_resid": info_ms["true_resid"]},
@@ -412,12 +439,17 @@ def run_gpu(args, rank, world, dist):
         "dslash_fp16_dagger": {"kernel": "hop2_kernel<F16,DAG=1,PRE=0>", "us": round(t_hop16 * 1e6, 2),
                                "alg_bytes": alg16, "gbs": round(alg16 / t_hop16 / 1e9, 1),
                                "frac": round(alg16 / t_hop16 / 1e9 / peak, 4)},
-        # traffic: dram read + write of this kernel from one ncu capture of
-        # `bench.py --dslash-only` (profiles/hop_fp32_mobius_16x16x16x32_Ls12.md)
-        "roofline": {"bound": "hbm", "achieved": round(hop_gbs, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(hop_gbs / peak, 4), "traffic": HOP_FP32_DRAM_BYTES,
-                     "kernel": "hop2_kernel<F32,0,1,0>", "peak_kind": kind,
-                     "alg_bytes_per_launch": alg_bytes},
+        # the dominant kernel of the timed MSPCG solves (hop-kernel timer):
+        # achieved = compulsory bytes / device time over all its launches in
+        # the timed region; traffic = dram read + write per launch from one
+        # ncu capture of the same bench command (profiles/), null if none
+        "roofline": {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(dom_gbs / peak, 4), "traffic": dom_traffic,
+                     "kernel": dom["name"], "peak_kind": kind, "launches": dom["launches"],
+                     "share_of_timed_solves": round(dom["seconds"] / t_steps, 4),
+                     "avg_launch_us": round(dom["seconds"] / dom["launches"] * 1e6, 2),
+                     "alg_bytes_per_launch": int(dom["alg_bytes"] / dom["launches"])},
+        "hop_kernels_in_timed_solves": kernels,
         "e2e": {"value": round(t_e2e, 6), "unit": "s",
                 "h2d_bytes_per_step": int(bh.numel() * 16), "d2h_bytes_per_step": int(xh.numel() * 16)},
         "gpu_launches": int(launches_ms),

@@ -132,6 +132,18 @@ typedef struct {
   double seconds;        /* wall time of the whole call (same for all rhs)   */
 } dwf_solve_info;
 
+/* Device time of one hop-kernel family, from dwf_profile_read. */
+typedef struct {
+  char name[48];       /* kernel and template arguments, e.g.
+                        * "hop2_kernel<F16,1,0,0,1>" (S, DAG, PRE, RECON, EPI) */
+  long long launches;  /* launches since profiling was (re)enabled            */
+  double seconds;      /* sum over launches of (exit of the last CTA to
+                        * finish - entry of CTA 0), from the global timer     */
+  double alg_bytes;    /* compulsory bytes summed over the launches: every
+                        * output, input, added and dotted element once and
+                        * the links of the output and input sites            */
+} dwf_kernel_time;
+
 typedef struct dwf_ctx dwf_ctx;
 
 /* Create a context on CUDA device `device` for action `a`.
@@ -305,6 +317,24 @@ dwf_status dwf_autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const doubl
 dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs,
                        const double *mf, const dwf_solver_params *params,
                        dwf_solve_info *info, void *stream);
+
+/* Kernel timer for the Dslash (hop) kernels, the operator applications of
+ * paper Sec. 2.2 that every solver step is made of (no counterpart in the
+ * paper: measurement only). on = 1 turns it on and resets every counter;
+ * on = 0 turns it off (counters kept). While on, every hop launch on this
+ * context records its span with the GPU's global timer (read by CTA 0 at
+ * entry and by the last CTA to finish at exit; one atomic per CTA) into one
+ * of 32 slots keyed by (precision, adjoint, M_phi on load, Ls epilogue); the
+ * outer-iteration CUDA graphs are re-captured with the timer in them. Hop launches of one context
+ * must not overlap in time while it is on (use one stream at a time).
+ * Synchronises the device. Errors: INVALID_ARG, CUDA. */
+dwf_status dwf_profile_enable(dwf_ctx *ctx, int on);
+
+/* Copy the non-empty timer slots into out[0 .. min(*n, cap) - 1] (host array
+ * of cap entries; may be NULL when cap = 0) and set *n to the number of
+ * non-empty slots. Synchronises the device. Nothing is recorded unless
+ * dwf_profile_enable(ctx, 1) was called. Errors: INVALID_ARG, CUDA. */
+dwf_status dwf_profile_read(dwf_ctx *ctx, dwf_kernel_time *out, int cap, int *n);
 
 #ifdef __cplusplus
 }

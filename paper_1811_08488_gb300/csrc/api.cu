@@ -1,4 +1,5 @@
 // The C ABI (include/dwf.h): argument checks, context management, dispatch.
+#include <cstdio>
 #include <cstring>
 #include <exception>
 
@@ -272,6 +273,66 @@ dwf_status dwf_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even
   dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
   dwf::apply_odd_reconstruct(ctx, psi_odd, psi_even, phi_odd, prec, nrhs, mf, w,
                              (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+// Name of the kernel behind profiler slot `slot` (prec * 8 + DAG * 4 + PRE * 2
+// + EPI) in this context: hop2_kernel for FP32/FP16/BF16 with even Ls,
+// hop_kernel otherwise; the template arguments as the kernel declares them.
+static std::string prof_slot_name(const dwf_ctx *ctx, int slot) {
+  static const char *kS[4] = {"F64", "F32", "F16", "BF16"};
+  const int p = slot / 8, dag = (slot >> 2) & 1, pre = (slot >> 1) & 1, epi = slot & 1;
+  const int rc = (p != DWF_FP64 && ctx->act.recon12) ? 1 : 0;
+  char buf[64];
+  if (p != DWF_FP64 && ctx->act.Ls % 2 == 0)
+    std::snprintf(buf, sizeof buf, "hop2_kernel<%s,%d,%d,%d,%d>", kS[p], dag, pre, rc, epi);
+  else
+    std::snprintf(buf, sizeof buf, "hop_kernel<%s,%d,%d,%d>%s", kS[p], dag, pre, rc,
+                  epi ? " +Ls epilogue" : "");
+  return buf;
+}
+
+dwf_status dwf_profile_enable(dwf_ctx *ctx, int on) {
+  if (!ctx) return DWF_ERR_INVALID_ARG;
+  API_TRY(ctx)
+  DWF_REQUIRE(on == 0 || on == 1, DWF_ERR_INVALID_ARG, "on must be 0 or 1");
+  DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (on) {
+    ctx->prof.ensure(sizeof(dwf::KernProf) * dwf::kProfSlots);
+    dwf::KernProf init[dwf::kProfSlots];
+    std::memset(init, 0, sizeof init);
+    DWF_CUDA_TRY(cudaDeviceSynchronize());
+    DWF_CUDA_TRY(cudaMemcpy(ctx->prof.p, init, sizeof init, cudaMemcpyHostToDevice));
+  }
+  ctx->prof_on = on;
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_profile_read(dwf_ctx *ctx, dwf_kernel_time *out, int cap, int *n) {
+  if (!ctx) return DWF_ERR_INVALID_ARG;
+  API_TRY(ctx)
+  DWF_REQUIRE(n != nullptr, DWF_ERR_INVALID_ARG, "null count");
+  DWF_REQUIRE(cap >= 0 && (cap == 0 || out != nullptr), DWF_ERR_INVALID_ARG,
+              "null output array");
+  *n = 0;
+  if (ctx->prof.p) {
+    DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+    dwf::KernProf k[dwf::kProfSlots];
+    DWF_CUDA_TRY(cudaDeviceSynchronize());
+    DWF_CUDA_TRY(cudaMemcpy(k, ctx->prof.p, sizeof k, cudaMemcpyDeviceToHost));
+    for (int s = 0; s < dwf::kProfSlots; ++s) {
+      if (k[s].launches == 0) continue;
+      if (*n < cap) {
+        dwf_kernel_time &o = out[*n];
+        std::memset(&o, 0, sizeof o);
+        std::snprintf(o.name, sizeof o.name, "%s", prof_slot_name(ctx, s).c_str());
+        o.launches = (long long)k[s].launches;
+        o.seconds = (double)k[s].total_ns * 1e-9;
+        o.alg_bytes = (double)k[s].bytes;
+      }
+      ++*n;
+    }
+  }
   API_CATCH(ctx)
 }
 

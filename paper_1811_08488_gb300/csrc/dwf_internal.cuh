@@ -133,6 +133,17 @@ inline void finalize_coef(LsCoef &c) {
          (float)c.a1, (float)c.mf, (float)c.pre_b, (float)c.pre_c, (float)c.q0};
 }
 
+// Device-side timer of one kernel family (slot), filled while profiling is
+// on: start holds the entry time of CTA 0 of the launch in flight (global
+// timer, ns), done counts its finished CTAs; the last CTA adds its exit time
+// minus start to total_ns and resets done for the next launch (end unused).
+struct KernProf {
+  unsigned long long start, end;
+  unsigned long long total_ns, launches, bytes;
+  unsigned int done, pad;
+};
+constexpr int kProfSlots = 32;  // prec * 8 + DAG * 4 + PRE * 2 + EPI
+
 struct HopParams {
   FieldRef in, out, xown, dotv;
   const char *links = nullptr;
@@ -157,6 +168,8 @@ struct HopParams {
   int dot_rstride = 0;
   unsigned int *counters = nullptr;  // [rhs][block]
   const int *skip = nullptr;    // per rhs: nonzero = skip (converged)
+  KernProf *prof = nullptr;     // timer slot of this launch (null: profiling off)
+  unsigned long long alg_bytes = 0;  // compulsory bytes of this launch
   LsCoef coef[kMaxRhs];
 };
 
@@ -251,6 +264,8 @@ struct dwf_ctx {
   std::map<std::string, std::unique_ptr<dwf::BlockPlan>> block_plans;
   std::map<std::string, std::unique_ptr<dwf::SolverPlan>> solver_plans;
   std::map<std::string, std::array<int, 4>> tuned_blocks;  // autotuner results
+  dwf::DevBuf prof;    // kProfSlots KernProf timer slots of the hop kernels
+  int prof_on = 0;
   ~dwf_ctx();
 };
 

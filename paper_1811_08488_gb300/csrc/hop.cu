@@ -186,9 +186,46 @@ __device__ __forceinline__ void hop_dot(const HopParams &P, double d, double *re
     P.dot_out[(size_t)rhs * P.dot_rstride + blk] = total;
 }
 
+// Kernel timer (only when P.prof is set). CTA 0 reads the global timer at
+// entry (CTAs are dispatched in index order, so it starts first); every CTA
+// takes a ticket when it has finished, and the CTA with the last ticket reads
+// the timer again, adds the span to the slot and resets it for the next
+// launch. One atomic per CTA. Launches of one slot must not overlap in time
+// (one stream at a time), which stream order guarantees.
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool first_cta() {
+  return blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+}
+__device__ __noinline__ void prof_enter(const HopParams &P) {
+  if (P.prof && threadIdx.x == 0 && first_cta()) {
+    P.prof->start = gtimer_ns();
+    __threadfence();
+  }
+}
+__device__ __noinline__ void prof_exit(const HopParams &P) {
+  if (!P.prof) return;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  KernProf *k = P.prof;
+  const unsigned int nct = gridDim.x * gridDim.y * gridDim.z;
+  if (atomicAdd(&k->done, 1u) != nct - 1) return;
+  __threadfence();
+  const unsigned long long t1 = gtimer_ns();
+  const unsigned long long t0 = *reinterpret_cast<volatile unsigned long long *>(&k->start);
+  k->total_ns += t1 - t0;
+  k->launches += 1;
+  k->bytes += P.alg_bytes;
+  k->done = 0;
+  __threadfence();
+}
+
 // One thread per output (site, s): used for FP64 fields and odd Ls.
 template <class S, bool DAG, bool PRE, bool RC>
-__global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopParams P) {
+__device__ __forceinline__ void hop_body(const HopParams &P) {
   using R = typename S::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -266,6 +303,13 @@ __global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopPar
     }
     hop_dot(P, d, red, rhs, blk);
   }
+}
+
+template <class S, bool DAG, bool PRE, bool RC>
+__global__ void __launch_bounds__(256) hop_kernel(const __grid_constant__ HopParams P) {
+  prof_enter(P);
+  hop_body<S, DAG, PRE, RC>(P);
+  prof_exit(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -451,7 +495,7 @@ __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const c
 // EPI: the Ls epilogue is compiled in (its column registers would otherwise
 // weigh on the plain hop's register allocation).
 template <class S, bool DAG, bool PRE, bool RC, bool EPI>
-__global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ HopParams P) {
+__device__ __forceinline__ void hop2_body(const HopParams &P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const int rhs = blockIdx.z, blk = blockIdx.y;
@@ -548,6 +592,13 @@ __global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ Ho
     }
     hop_dot(P, d, red, rhs, blk);
   }
+}
+
+template <class S, bool DAG, bool PRE, bool RC, bool EPI>
+__global__ void __launch_bounds__(128, 4) hop2_kernel(const __grid_constant__ HopParams P) {
+  prof_enter(P);
+  hop2_body<S, DAG, PRE, RC, EPI>(P);
+  prof_exit(P);
 }
 
 // Two slices per thread for FP32/FP16/BF16 with even Ls; one otherwise.

@@ -36,7 +36,24 @@ OpWork op_work(dwf_ctx *ctx, dwf_prec p, int nrhs) {
   return w;
 }
 
-static void launch(dwf_prec p, const HopParams &P, int dag, int pre, int nrhs, cudaStream_t st) {
+// Compulsory bytes of one hop launch: every output, input (and added x or
+// dot vector) element once, and the links of the output and input sites.
+static unsigned long long hop_alg_bytes(dwf_prec p, const HopParams &P, int nrhs) {
+  const unsigned long long eb = p == DWF_FP64 ? 192 : p == DWF_FP32 ? 96 : 52;
+  const unsigned long long lb = (P.recon ? 12 : 18) * (p == DWF_FP64 ? 8 : p == DWF_FP32 ? 4 : 2);
+  const unsigned long long elems = (unsigned long long)P.n_out + P.in_limit +
+                                   (P.has_x ? P.xown_limit : 0) + (P.dot ? P.n_out : 0);
+  return (unsigned long long)P.nblocks *
+         (elems * P.Ls * eb * nrhs + ((unsigned long long)P.n_out + P.in_limit) * 4 * lb);
+}
+
+static void launch(dwf_ctx *ctx, dwf_prec p, const HopParams &P0, int dag, int pre, int nrhs,
+                   cudaStream_t st) {
+  HopParams P = P0;
+  if (ctx->prof_on) {
+    P.prof = ctx->prof.as<KernProf>() + (int)p * 8 + dag * 4 + pre * 2 + (P.epi ? 1 : 0);
+    P.alg_bytes = hop_alg_bytes(p, P, nrhs);
+  }
   switch (p) {
     case DWF_FP64: launch_hop<F64>(P, dag, pre, nrhs, st); break;
     case DWF_FP32: launch_hop<F32>(P, dag, pre, nrhs, st); break;
@@ -87,7 +104,7 @@ void apply_dslash(dwf_ctx *ctx, void *out, const void *in, int out_parity, int d
     }
   }
   P.epi = dagger ? 1 : 0;
-  launch(p, P, dagger, dagger ? 0 : 1, nrhs, st);
+  launch(ctx, p, P, dagger, dagger ? 0 : 1, nrhs, st);
 }
 
 // First half of D_PC (or D_PC^+): u(odd) = K (-1/2 Dhop M_phi in) with
@@ -102,7 +119,7 @@ static void mpc_first(dwf_ctx *ctx, void *odd_out, const void *in, int dagger, d
   P.epi = 1;
   P.inv = 1;
   P.skip = skip;
-  launch(p, P, dagger, dagger ? 0 : 1, nrhs, st);
+  launch(ctx, p, P, dagger, dagger ? 0 : 1, nrhs, st);
 }
 
 // Second half: out(even) = M_5 in + 1/2 Dhop u, or M_5^+ in + 1/2 M_phi^+ Dhop^+ v.
@@ -129,7 +146,7 @@ static void mpc_second(dwf_ctx *ctx, void *out, const void *odd_in, const void *
     P.dot_out = dot->dot_out;
     P.dot_rstride = dot->dot_rstride;
   }
-  launch(p, P, dagger, 0, nrhs, st);
+  launch(ctx, p, P, dagger, 0, nrhs, st);
 }
 
 void apply_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
@@ -161,7 +178,7 @@ void apply_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even, const v
   }
   P.epi = 1;
   P.has_x = 1;
-  launch(p, P, 0, 0, nrhs, st);
+  launch(ctx, p, P, 0, 0, nrhs, st);
   apply_mpc(ctx, b_even, w.y, 1, p, nrhs, mf, w, st);
 }
 
@@ -182,7 +199,7 @@ void apply_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
   }
   P.epi = 1;
   P.has_x = 1;
-  launch(p, P, 0, 1, nrhs, st);
+  launch(ctx, p, P, 0, 1, nrhs, st);
   LsCoef c[kMaxRhs];
   for (int r = 0; r < nrhs; ++r) c[r] = coef_m5inv(ctx->act, mf[r], 1.0);
   launch_ls_op(p, static_cast<char *>(psi_odd), w.u, (long long)field_rhs_bytes(p, Vh, Ls), Vh,
@@ -325,7 +342,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
     P.coef[r] = coef_k(a, mf[r], -0.5);
     with_pre(P.coef[r], a);
   }
-  launch(bp->inner, P, 0, 1, nrhs, st);
+  launch(ctx, bp->inner, P, 0, 1, nrhs, st);
 
   // hop 2: even (distance <= 2) <- odd; y = M_5 p + 1/2 Dhop u1  (= D_PC P_s p)
   P = base;
@@ -345,7 +362,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
     P.coef[r].a0 = alpha_of(a);
     P.coef[r].a1 = beta_of(a);
   }
-  launch(bp->inner, P, 0, 0, nrhs, st);
+  launch(ctx, bp->inner, P, 0, 0, nrhs, st);
 
   // hop 3: odd (distance <= 1) <- even (distance <= 2); u2 = K^+ (-1/2 Dhop^+ y)
   P = base;
@@ -358,7 +375,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   P.in_link_off = 0;
   P.inv = 1;
   for (int r = 0; r < nrhs; ++r) P.coef[r] = coef_k(a, mf[r], -0.5);
-  launch(bp->inner, P, 1, 0, nrhs, st);
+  launch(ctx, bp->inner, P, 1, 0, nrhs, st);
 
   // hop 4: even block sites <- odd; Ap = M_5^+ y + 1/2 M_phi^+ Dhop^+ u2
   P = base;
@@ -385,7 +402,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
     P.dot_out = bp->scal.as<double>() + 2 * (size_t)bp->nrhs * g.nblocks;  // pAp
     P.dot_rstride = g.nblocks;
   }
-  launch(bp->inner, P, 1, 0, nrhs, st);
+  launch(ctx, bp->inner, P, 1, 0, nrhs, st);
 }
 
 BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double *rz_out,
@@ -620,7 +637,7 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   if (use_graph) {
     std::ostringstream key;
     key << (void *)bp << "/" << (bp ? bp->r.p : nullptr) << "/" << prm->inner_iters << "/"
-        << prm->snake << "/" << plain << "/" << A.flexible;
+        << prm->snake << "/" << plain << "/" << A.flexible << "/" << ctx->prof_on;
     for (int r = 0; r < nrhs; ++r) key << "/" << mf[r];
     if (!sp->graph || sp->graph_key != key.str()) {
       if (sp->graph) cudaGraphExecDestroy(sp->graph);

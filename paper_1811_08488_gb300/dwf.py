@@ -31,7 +31,7 @@ EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_def
            "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_m5inv_gemm", "dwf_mpc", "dwf_mdagm", "dwf_mdagm_noalloc",
            "dwf_block_apply",
            "dwf_block_precond", "dwf_autotune_block", "dwf_source_prep", "dwf_odd_reconstruct",
-           "mspcg_solve"]
+           "mspcg_solve", "dwf_profile_enable", "dwf_profile_read"]
 
 
 class DwfError(RuntimeError):
@@ -61,6 +61,15 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("seconds", C.c_double),
+                ("alg_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {"name": self.name.decode(), "launches": self.launches, "seconds": self.seconds,
+                "alg_bytes": self.alg_bytes}
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libdwf.so is not built ({path}); run __graft_entry__.build()")
@@ -88,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_block_apply": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "dwf_block_precond": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "mspcg_solve": (I, [P, P, P, I, D, C.POINTER(SolverParams), C.POINTER(SolveInfo), P]),
+        "dwf_profile_enable": (I, [P, I]),
+        "dwf_profile_read": (I, [P, C.POINTER(KernelTime), I, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +308,18 @@ class Context:
         psi_o = torch.zeros_like(phi_odd)
         self.field_export(psi_o, nat["xo"], "fp64", nrhs)
         return psi_e, psi_o, st, info
+
+    def profile(self, on=True):
+        """dwf_profile_enable: turn the hop-kernel timer on (resetting it) or off."""
+        self._check(lib().dwf_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """dwf_profile_read: [{name, launches, seconds, alg_bytes}] per timed kernel."""
+        n = C.c_int(0)
+        self._check(lib().dwf_profile_read(self._h, None, 0, C.byref(n)))
+        out = (KernelTime * max(1, n.value))()
+        self._check(lib().dwf_profile_read(self._h, out, n.value, C.byref(n)))
+        return [out[i].as_dict() for i in range(n.value)]
 
     def autotune_block(self, b, mf, params, trial=20, stream=None):
         """dwf_autotune_block: returns (block shape, predicted seconds)."""
