@@ -81,7 +81,7 @@ extern "C" {
 typedef enum {
   DWF_OK = 0,
   DWF_ERR_INVALID_ARG = 1,   /* bad pointer, size, shape or parameter        */
-  DWF_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement  */
+  DWF_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement */
   DWF_ERR_CUDA = 3,          /* a CUDA call failed; see dwf_last_error        */
   DWF_ERR_NOT_CONVERGED = 4, /* maxiter reached; x and info are still filled  */
   DWF_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired            */
