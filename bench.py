@@ -39,8 +39,8 @@ METRIC = "MSPCG vs plain CG time-to-solve at resid 1e-10 (1 GB300); Dslash HBM G
 # inside the MSPCG solve of this workload, from one ncu capture of the same
 # bench command on the current kernels (see profiles/); a kernel missing here
 # reports traffic null. hop2_kernel<F16,1,0,0,1>: block-operator hops 4 and 3,
-# (185.44 + 26.23) and (174.97 + 49.51) MB, mean of the two launches.
-DRAM_BYTES_PER_LAUNCH = {"hop2_kernel<F16,1,0,0,1>": 218071680}
+# (185.43 + 26.95) and (174.87 + 49.17) MB, mean of the two launches.
+DRAM_BYTES_PER_LAUNCH = {"hop2_kernel<F16,1,0,0,1>": 218210560}
 WORKLOAD = "mobius_16^3x32x12"
 
 

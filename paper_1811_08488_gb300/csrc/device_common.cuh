@@ -187,6 +187,41 @@ __device__ __forceinline__ void load24x2(const char *base, long long soff, int c
   }
 }
 
+// One chirality (UPPER: reals 0..11, else 12..23) of elements e (v0) and e+1
+// (v1); e even. FP32/FP16/BF16, 256-bit loads as in load24x2.
+template <class S, bool UPPER>
+__device__ __forceinline__ void load12x2(const char *base, long long soff, int cs, int e,
+                                         float *v0, float *v1) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(base) + e;
+  if constexpr (std::is_same<S, F32>::value) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint32_t a[8];
+      ldg256(p + (size_t)(UPPER ? k : 3 + k) * cs, a);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v0[4 * k + i] = __uint_as_float(a[i]);
+        v1[4 * k + i] = __uint_as_float(a[4 + i]);
+      }
+    }
+  } else {
+    const float2 scl = __ldg(reinterpret_cast<const float2 *>(base + soff) + e / 2);
+    float t0[16], t1[16];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      uint32_t a[8];
+      ldg256(p + (size_t)(UPPER ? k : 1 + k) * cs, a);
+      unpack8<S>(make_uint4(a[0], a[1], a[2], a[3]), t0 + 8 * k);
+      unpack8<S>(make_uint4(a[4], a[5], a[6], a[7]), t1 + 8 * k);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      v0[k] = t0[UPPER ? k : 4 + k] * scl.x;
+      v1[k] = t1[UPPER ? k : 4 + k] * scl.y;
+    }
+  }
+}
+
 // FP16/BF16: the stored values of elements e and e+1 (e even) without their
 // scales, which are returned in scl (the caller folds them in later).
 template <class S>

@@ -492,6 +492,51 @@ __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const c
                                      lmu + P.in_link_off + jb, ls, cf);
 }
 
+// The x-term of the Ls epilogue, out += (a0 + a1 S) x, on the thread's slices
+// s0 and s0 + 1 (o0, o1), added after the column walk. S is the walk's chiral
+// shift: (S x)_s = x_{s-1} with (S x)_0 = -mf x_{Ls-1} on the components the
+// walk runs down (the upper spin components of the operator, the lower ones
+// of its adjoint), (S x)_s = x_{s+1} with (S x)_{Ls-1} = -mf x_0 on the
+// others. Besides the pair it needs the down half of x at s0 - 1 and the up
+// half at s0 + 2.
+template <class S, bool DAG>
+__device__ __forceinline__ void add_x_term2(float *o0, float *o1, const char *x, long long soff,
+                                            int cs, int site, int s0, int Ls,
+                                            const LsK<float> &c) {
+  float x0[12], x1[12], w[12];
+  const int e = site * Ls + s0;
+  const float a0 = c.a0, a1 = c.a1, mf = c.mf;
+  const int sm = s0 == 0 ? Ls - 1 : s0 - 1;
+  const int sp = s0 + 2 == Ls ? 0 : s0 + 2;
+  const float fm = s0 == 0 ? -mf : 1.f, fp = s0 + 2 == Ls ? -mf : 1.f;
+  // upper components: down for the operator, up for its adjoint
+  load12x2<S, true>(x, soff, cs, e, x0, x1);
+  load12<S, true>(x, soff, cs, site * Ls + (DAG ? sp : sm), w);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    if (!DAG) {
+      o0[k] += a0 * x0[k] + a1 * (fm * w[k]);
+      o1[k] += a0 * x1[k] + a1 * x0[k];
+    } else {
+      o0[k] += a0 * x0[k] + a1 * x1[k];
+      o1[k] += a0 * x1[k] + a1 * (fp * w[k]);
+    }
+  }
+  // lower components: up for the operator, down for its adjoint
+  load12x2<S, false>(x, soff, cs, e, x0, x1);
+  load12<S, false>(x, soff, cs, site * Ls + (DAG ? sm : sp), w);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    if (!DAG) {
+      o0[12 + k] += a0 * x0[k] + a1 * x1[k];
+      o1[12 + k] += a0 * x1[k] + a1 * (fp * w[k]);
+    } else {
+      o0[12 + k] += a0 * x0[k] + a1 * (fm * w[k]);
+      o1[12 + k] += a0 * x1[k] + a1 * x0[k];
+    }
+  }
+}
+
 // EPI: the Ls epilogue is compiled in (its column registers would otherwise
 // weigh on the plain hop's register allocation).
 template <class S, bool DAG, bool PRE, bool RC, bool EPI>
@@ -535,38 +580,27 @@ __device__ __forceinline__ void hop2_body(const HopParams &P) {
   if constexpr (EPI) {
     const int col = Ls + 1;
     float *T = reinterpret_cast<float *>(smem_raw);
-    float *X = T + nsites * 24 * col;
     if (active) {
 #pragma unroll
       for (int k = 0; k < 24; ++k) {
         T[(sl * 24 + k) * col + s0] = a0[k];
         T[(sl * 24 + k) * col + s0 + 1] = a1[k];
       }
-      if (P.has_x) {
-        float x0[24], x1[24];
-        if (site < P.xown_limit) {
-          const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
-          load24x2<S>(xo, P.xown.scale_off, P.xown.cs, e, x0, x1);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 24; ++k) x0[k] = x1[k] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 24; ++k) {
-          X[(sl * 24 + k) * col + s0] = x0[k];
-          X[(sl * 24 + k) * col + s0 + 1] = x1[k];
-        }
-      }
     }
     __syncthreads();
-    epilogue_columns<float>(T, P.has_x ? X : nullptr, nsites, site0, P.n_out, Ls, DAG, P.inv,
-                            cf);
+    epilogue_columns<float>(T, nullptr, nsites, site0, P.n_out, Ls, DAG, P.inv, cf);
     __syncthreads();
     if (active) {
 #pragma unroll
       for (int k = 0; k < 24; ++k) {
         a0[k] = T[(sl * 24 + k) * col + s0];
         a1[k] = T[(sl * 24 + k) * col + s0 + 1];
+      }
+      // the x-term after the column walk, in registers (no shared-memory copy
+      // of x, which would take L1 capacity from the gather)
+      if (P.has_x && site < P.xown_limit) {
+        const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
+        add_x_term2<S, DAG>(a0, a1, xo, P.xown.scale_off, P.xown.cs, site, s0, Ls, cf.f);
       }
     }
   } else {
@@ -616,7 +650,9 @@ int hop_sites_per_cta(int Ls, dwf_prec p) {
 size_t hop_smem_bytes(int Ls, dwf_prec p, int epi, int has_x) {
   if (!epi) return 0;
   const size_t rs = (p == DWF_FP64) ? 8 : 4;
-  return (size_t)hop_sites_per_cta(Ls, p) * 24 * (Ls + 1) * rs * (has_x ? 2 : 1);
+  // the two-slice kernel adds x in registers; the one-slice kernel stages it
+  const int xbuf = (has_x && !hop_pairs(Ls, p)) ? 2 : 1;
+  return (size_t)hop_sites_per_cta(Ls, p) * 24 * (Ls + 1) * rs * xbuf;
 }
 
 template <class S, bool DAG, bool PRE, bool RC>
