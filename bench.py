@@ -446,6 +446,7 @@ def run_gpu(args, rank, world, dist):
         # ncu capture of the same bench command (profiles/), null if none
         "roofline": {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(dom_gbs / peak, 4), "traffic": dom_traffic,
+                     "frac_of_8tbs_nominal": round(dom_gbs / 8000, 4),
                      "kernel": dom["name"], "peak_kind": kind, "launches": dom["launches"],
                      "share_of_timed_solves": round(dom["seconds"] / t_steps, 4),
                      "avg_launch_us": round(dom["seconds"] / dom["launches"] * 1e6, 2),
