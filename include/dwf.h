@@ -116,7 +116,8 @@ typedef struct {
   int snake;          /* 1: A_s = P_s A P_s (snake terms), 0: per-hop Dirichlet */
   int use_graph;      /* 1: replay the iteration from a captured CUDA graph     */
   int io_on_host;     /* mspcg_solve: 1 = x and b are host pointers             */
-  int check_every;    /* outer iterations between host convergence checks      */
+  int check_every;    /* outer iterations between host convergence checks,    
+                       * 1 .. 256                                             */
   int flexible;       /* 1: flexible PCG, beta = <r_new - r, z_new> / <r, z>    
                        * (Polak-Ribiere); 0: Algorithm 1's <r_new, z_new> /   
                        * <r, z> (Fletcher-Reeves)                             */
@@ -130,6 +131,11 @@ typedef struct {
   int converged;         /* 1 when true_resid <= tol                         */
   double true_resid;     /* |b - A x| / |b| recomputed in FP64               */
   double seconds;        /* wall time of the whole call (same for all rhs)   */
+  double dslash_gbs;     /* compulsory bytes of the outer operator's hop     
+                          * launches in params->outer precision during this 
+                          * call, over their device time (GB/s; same for all
+                          * rhs), from the hop-kernel timer; -1 when the     
+                          * timer is off (dwf_profile_enable)               */
 } dwf_solve_info;
 
 /* Device time of one hop-kernel family, from dwf_profile_read. */
@@ -165,8 +171,10 @@ const char *dwf_last_error(const dwf_ctx *ctx);
  * delta 0.001, snake 1, use_graph 1, io_on_host 0, check_every 10, flexible 0. */
 void dwf_solver_params_default(dwf_solver_params *p);
 
-/* Load the gauge field U (layout above; host pointer if on_device == 0).
- * Packs FP64, FP32 and FP16 copies of the links with the antiperiodic time
+/* Load the gauge field U (layout above; host pointer if on_device == 0): the
+ * SU(3) links U_mu(x) of the Wilson hop D^w in M^4 = D^w M_phi (paper Sec.
+ * 2.2, the definition of D^w). The caller keeps ownership of U; the context
+ * copies it. Packs FP64, FP32 and FP16 copies of the links with the antiperiodic time
  * sign folded into the links that cross t = Lt-1 -> 0, and invalidates every
  * cached block plan. Synchronous. Errors: INVALID_ARG (NULL U), CUDA. */
 dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device);

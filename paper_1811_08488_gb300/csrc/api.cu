@@ -16,7 +16,13 @@ dwf_ctx::~dwf_ctx() {
   if (own_stream) cudaStreamDestroy(own_stream);
 }
 
-#define API_TRY(ctx) try {
+// Every entry point on a context fails once a bounded device wait expired with
+// device work possibly still in flight (the context must be destroyed).
+#define API_TRY(ctx)                                                     \
+  try {                                                                  \
+    if ((ctx) && (ctx)->unusable)                                        \
+      throw Error{DWF_ERR_TIMEOUT,                                       \
+                  "the context is unusable after an expired device wait; destroy it"};
 #define API_CATCH(ctx)                                                   \
   }                                                                      \
   catch (const Error &e) {                                               \
@@ -276,11 +282,14 @@ dwf_status dwf_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even
   API_CATCH(ctx)
 }
 
-// Name of the kernel behind profiler slot `slot` (prec * 8 + DAG * 4 + PRE * 2
-// + EPI) in this context: hop2_kernel for FP32/FP16/BF16 with even Ls,
-// hop_kernel otherwise; the template arguments as the kernel declares them.
+// Name of the kernel behind profiler slot `slot` (role * 32 + prec * 8 + DAG * 4
+// + PRE * 2 + EPI) in this context: hop2_kernel for FP32/FP16/BF16 with even
+// Ls, hop_kernel otherwise; the template arguments as the kernel declares
+// them, and " [block]" for launches of the block operator A_s.
 static std::string prof_slot_name(const dwf_ctx *ctx, int slot) {
   static const char *kS[4] = {"F64", "F32", "F16", "BF16"};
+  const int role = slot / 32;
+  slot %= 32;
   const int p = slot / 8, dag = (slot >> 2) & 1, pre = (slot >> 1) & 1, epi = slot & 1;
   const int rc = (p != DWF_FP64 && ctx->act.recon12) ? 1 : 0;
   char buf[64];
@@ -289,7 +298,7 @@ static std::string prof_slot_name(const dwf_ctx *ctx, int slot) {
   else
     std::snprintf(buf, sizeof buf, "hop_kernel<%s,%d,%d,%d>%s", kS[p], dag, pre, rc,
                   epi ? " +Ls epilogue" : "");
-  return buf;
+  return std::string(buf) + (role ? " [block]" : "");
 }
 
 dwf_status dwf_profile_enable(dwf_ctx *ctx, int on) {
@@ -394,7 +403,8 @@ dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const dou
   check_params(params);
   DWF_REQUIRE(x && b, DWF_ERR_INVALID_ARG, "null x or b");
   DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
-  DWF_REQUIRE(params->check_every >= 1, DWF_ERR_INVALID_ARG, "check_every must be >= 1");
+  DWF_REQUIRE(params->check_every >= 1 && params->check_every <= dwf::kHistory,
+              DWF_ERR_INVALID_ARG, "check_every must be in 1 .. 256");
   DWF_REQUIRE(params->delta > 0 && params->delta < 1, DWF_ERR_INVALID_ARG,
               "delta must be in (0, 1)");
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->own_stream;

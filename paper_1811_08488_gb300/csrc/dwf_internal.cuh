@@ -142,7 +142,9 @@ struct KernProf {
   unsigned long long total_ns, launches, bytes;
   unsigned int done, pad;
 };
-constexpr int kProfSlots = 32;  // prec * 8 + DAG * 4 + PRE * 2 + EPI
+// slot = role * 32 + prec * 8 + DAG * 4 + PRE * 2 + EPI; role 0: operators on the
+// whole lattice (dslash, D_PC, A), role 1: the block operator A_s
+constexpr int kProfSlots = 64;
 
 struct HopParams {
   FieldRef in, out, xown, dotv;
@@ -159,6 +161,7 @@ struct HopParams {
   int Ls = 0;
   int nsites = 0;  // output sites per CTA (set by the launcher)
   int nblocks = 1;
+  int role = 0;    // timer slot group: 0 whole-lattice operator, 1 block operator
   int epi = 0;     // 0: out = q0 * acc; 1: Ls epilogue in shared memory
   int inv = 0;     // epilogue uses (1 - r S)^-1
   int has_x = 0;   // epilogue adds (a0 + a1 S) xown
@@ -266,6 +269,7 @@ struct dwf_ctx {
   std::map<std::string, std::array<int, 4>> tuned_blocks;  // autotuner results
   dwf::DevBuf prof;    // kProfSlots KernProf timer slots of the hop kernels
   int prof_on = 0;
+  int unusable = 0;    // set after a device wait expired with work possibly in flight
   ~dwf_ctx();
 };
 

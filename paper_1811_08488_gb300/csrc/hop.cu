@@ -174,6 +174,33 @@ __device__ __forceinline__ void epilogue_columns(R *T, const R *X, int nsites, i
   }
 }
 
+// One thread's part of the fused <dotv, out> of the global dot products. The
+// FP32 products are summed with Kahan compensation, so the sum's error is at
+// most about 3 * 2^-24 * sum |d_k a_k| (one rounding per product, two for the
+// compensated sum) whatever the count; the partials are then added in FP64.
+// FP64 fields sum in FP64.
+template <class R>
+__device__ __forceinline__ double dot_compensated(const R *d, const R *a, int n) {
+  if constexpr (std::is_same<R, double>::value) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k)
+      if (k < n) s += d[k] * a[k];
+    return s;
+  } else {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < 24; ++k)
+      if (k < n) {
+        const float y = d[k] * a[k] - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+      }
+    return (double)s - (double)c;
+  }
+}
+
 // Publish the CTA's part of Re<dotv, out> (both summed per (rhs, block)).
 __device__ __forceinline__ void hop_dot(const HopParams &P, double d, double *red, int rhs,
                                         int blk) {
@@ -296,10 +323,7 @@ __device__ __forceinline__ void hop_body(const HopParams &P) {
       R dv[24];
       const char *dp = P.dotv.data + blk * P.dotv.bstride + rhs * P.dotv.rstride;
       load24<S>(dp, P.dotv.scale_off, P.dotv.cs, e, dv);
-      R part = 0;
-#pragma unroll
-      for (int k = 0; k < 24; ++k) part += dv[k] * acc[k];
-      d = (double)part;
+      d = dot_compensated<R>(dv, acc, 24);
     }
     hop_dot(P, d, red, rhs, blk);
   }
@@ -619,10 +643,7 @@ __device__ __forceinline__ void hop2_body(const HopParams &P) {
       float d0[24], d1[24];
       const char *dp = P.dotv.data + blk * P.dotv.bstride + rhs * P.dotv.rstride;
       load24x2<S>(dp, P.dotv.scale_off, P.dotv.cs, e, d0, d1);
-      float part = 0.f;
-#pragma unroll
-      for (int k = 0; k < 24; ++k) part += d0[k] * a0[k] + d1[k] * a1[k];
-      d = (double)part;
+      d = dot_compensated<float>(d0, a0, 24) + dot_compensated<float>(d1, a1, 24);
     }
     hop_dot(P, d, red, rhs, blk);
   }

@@ -302,13 +302,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) m5inv_gemm_kernel(const __grid_
             smem_u32(mbar))
         : "memory");
   }
-  bool done = mbar_wait_bounded(smem_u32(mbar), 0, P.wait_ns);
+  const bool mma_done = __syncthreads_and(mbar_wait_bounded(smem_u32(mbar), 0, P.wait_ns));
   // test hook: the second phase is never completed (no further arrival), so
   // this wait runs out after the MMAs have finished (phase 0 above)
-  if (P.starve && done) done = mbar_wait_bounded(smem_u32(mbar), 1, P.wait_ns);
-  const bool ok = __syncthreads_and(done);
+  bool hook_ok = true;
+  if (P.starve && mma_done) hook_ok = mbar_wait_bounded(smem_u32(mbar), 1, P.wait_ns);
+  const bool ok = __syncthreads_and(mma_done && hook_ok);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok && tid == 0) atomicExch(P.status, 1);
+  // status 1: only the test hook's wait expired (the MMAs had completed);
+  // status 2: the MMA commit itself did not arrive in time, so MMAs may still
+  // be reading this CTA's shared memory and writing its TMEM columns
+  if (!ok && tid == 0) atomicMax(P.status, mma_done ? 1 : 2);
 
   if (ok) {
     // TMEM -> staging (the A region is free once the MMAs completed): warp w
@@ -510,7 +514,16 @@ void launch_m5inv_gemm(dwf_ctx *ctx, dwf_prec p, char *out, const char *in, int 
   int h_status = 0;
   DWF_CUDA_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   DWF_CUDA_TRY(cudaStreamSynchronize(st));
-  DWF_REQUIRE(h_status == 0, DWF_ERR_TIMEOUT, "tensor-core M_5^-1: a bounded wait expired");
+  if (h_status == 2) {
+    // after a genuine expiry the abandoned MMAs may still write TMEM and read
+    // shared memory that later CTAs reuse: nothing on this context is trusted
+    ctx->unusable = 1;
+    throw Error{DWF_ERR_TIMEOUT,
+                "tensor-core M_5^-1: the MMA completion wait expired; the context is unusable "
+                "and must be destroyed"};
+  }
+  DWF_REQUIRE(h_status == 0, DWF_ERR_TIMEOUT,
+              "tensor-core M_5^-1: a bounded wait expired after the MMAs completed");
 }
 
 }  // namespace dwf

@@ -51,6 +51,10 @@ extern "C" dwf_status dwf_mdagm_noalloc(dwf_ctx *ctx, void *out, const void *in,
     DWF_REQUIRE(ctx, DWF_ERR_INVALID_ARG, "null context");
     DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_RHS, DWF_ERR_INVALID_ARG, "nrhs out of range");
     DWF_REQUIRE(mf != nullptr, DWF_ERR_INVALID_ARG, "null mass array");
+    for (int r = 0; r < nrhs; ++r)
+      DWF_REQUIRE(mf[r] == mf[r], DWF_ERR_INVALID_ARG, "NaN quark mass");
+    DWF_REQUIRE(!ctx->unusable, DWF_ERR_TIMEOUT,
+                "the context is unusable after an expired device wait; destroy it");
     DWF_REQUIRE(prec == DWF_FP64 || prec == DWF_FP32, DWF_ERR_INVALID_ARG,
                 "operator entry points take DWF_FP64 or DWF_FP32 fields");
     DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");

@@ -51,7 +51,8 @@ static void launch(dwf_ctx *ctx, dwf_prec p, const HopParams &P0, int dag, int p
                    cudaStream_t st) {
   HopParams P = P0;
   if (ctx->prof_on) {
-    P.prof = ctx->prof.as<KernProf>() + (int)p * 8 + dag * 4 + pre * 2 + (P.epi ? 1 : 0);
+    P.prof = ctx->prof.as<KernProf>() + P.role * 32 + (int)p * 8 + dag * 4 + pre * 2 +
+             (P.epi ? 1 : 0);
     P.alg_bytes = hop_alg_bytes(p, P, nrhs);
   }
   switch (p) {
@@ -324,6 +325,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   base.nblocks = g.nblocks;
   base.skip = skip;
   base.epi = 1;
+  base.role = 1;
   const int odd_out = snake ? g.n_o1 : g.n_ob;
   const int even_mid = snake ? g.n_e2 : g.n_b;
   const int odd_in = snake ? g.n_o1 : g.n_ob;
@@ -567,9 +569,28 @@ static void enqueue_reliable_update(SolveSetup &S, cudaStream_t st) {
   }
 }
 
+// Compulsory bytes and device nanoseconds summed over the hop-kernel timer
+// slots of the whole-lattice operators in precision p (zero when the timer is
+// off). Waits for the work queued on st.
+static void outer_hop_totals(dwf_ctx *ctx, dwf_prec p, cudaStream_t st, double &bytes,
+                             double &ns) {
+  bytes = ns = 0.0;
+  if (!ctx->prof_on || !ctx->prof.p) return;
+  KernProf k[8];
+  DWF_CUDA_TRY(cudaStreamSynchronize(st));
+  DWF_CUDA_TRY(cudaMemcpy(k, ctx->prof.as<KernProf>() + (int)p * 8, sizeof k,
+                          cudaMemcpyDeviceToHost));
+  for (const KernProf &q : k) {
+    bytes += (double)q.bytes;
+    ns += (double)q.total_ns;
+  }
+}
+
 dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
                  const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st) {
   const auto t0 = std::chrono::steady_clock::now();
+  double hop_bytes0, hop_ns0;
+  outer_hop_totals(ctx, prm->outer, st, hop_bytes0, hop_ns0);
   const dwf_prec lo = prm->outer;
   DWF_REQUIRE(lo == DWF_FP32 || lo == DWF_FP64, DWF_ERR_INVALID_ARG,
               "outer precision must be FP64 or FP32");
@@ -740,7 +761,8 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
       }
     }
     if (status == DWF_ERR_NAN) break;
-    chunk = std::max(1, std::min(prm->check_every, min_pred));
+    // never more iterations between checks than the |r|^2 ring holds
+    chunk = std::max(1, std::min(std::min(prm->check_every, kHistory), min_pred));
     if (any_ru) {
       DWF_CUDA_TRY(cudaMemcpyAsync(sp->skip_ru.p, hs_ru, sizeof(int) * nrhs,
                                    cudaMemcpyHostToDevice, st));
@@ -796,6 +818,11 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   DWF_CUDA_TRY(cudaStreamSynchronize(st));
   const double secs =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  double hop_bytes1, hop_ns1;
+  outer_hop_totals(ctx, lo, st, hop_bytes1, hop_ns1);
+  const double dslash_gbs = (ctx->prof_on && hop_ns1 > hop_ns0)
+                                ? (hop_bytes1 - hop_bytes0) / (hop_ns1 - hop_ns0)
+                                : -1.0;
   bool all_conv = true;
   for (int r = 0; r < nrhs; ++r) {
     if (info) {
@@ -805,6 +832,7 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
       info[r].converged = final_res[r] >= 0 && final_res[r] <= prm->tol;
       info[r].true_resid = final_res[r];
       info[r].seconds = secs;
+      info[r].dslash_gbs = dslash_gbs;
     }
     all_conv &= final_res[r] >= 0 && final_res[r] <= prm->tol;
   }

@@ -55,7 +55,8 @@ class SolverParams(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int),
                 ("reliable_updates", C.c_int), ("converged", C.c_int),
-                ("true_resid", C.c_double), ("seconds", C.c_double)]
+                ("true_resid", C.c_double), ("seconds", C.c_double),
+                ("dslash_gbs", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -54,6 +54,39 @@ def test_binding_struct_layouts_match_header(libpath):
     assert p.flexible == 0
 
 
+def c_layout(struct, fields, tmp_path):
+    """sizeof(struct) and offsetof(struct, f) for each field, as a C compiler
+    lays them out from include/dwf.h."""
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"dwf.h\"\n"
+                   f"int main(void) {{\n  printf(\"%zu\\n\", sizeof({struct}));\n{body}"
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize("cname,pyname", [("dwf_action", "Action"),
+                                          ("dwf_solver_params", "SolverParams"),
+                                          ("dwf_solve_info", "SolveInfo"),
+                                          ("dwf_kernel_time", "KernelTime")])
+def test_binding_structs_match_the_c_layout(cname, pyname, tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that a
+    C compiler gives the header's struct (dwf_solve_info includes dslash_gbs)."""
+    from paper_1811_08488_gb300 import dwf
+    cls = getattr(dwf, pyname)
+    fields = [f for f, _ in cls._fields_]
+    size, offs = c_layout(cname, fields, tmp_path)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
+    if cname == "dwf_solve_info":
+        assert "dslash_gbs" in fields
+
+
 def test_no_cpu_fallback_without_device(libpath):
     """Without a usable GPU the context cannot be created: the library fails
     loudly instead of computing on the CPU."""

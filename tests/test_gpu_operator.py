@@ -4,10 +4,10 @@ Tolerances (relative, max-norm over the field):
 * FP64 paths: 1e-12.
 * FP32 paths: 1e-5 (one FP32 operator apply; the error is a few ulps of the
   largest terms, ~1e-6 relative).
-* FP16 / BF16 block storage: every stored spinor is rounded to 11 / 8
-  significant bits relative to its (site, s) maximum; four stored
-  intermediates give ~4 * 2^-11 ~ 2e-3 (FP16) and ~4 * 2^-8 ~ 1.6e-2 (BF16),
-  stated as 5e-3 and 4e-2 below.
+* FP16 / BF16 fields: every stored spinor is rounded to 11 / 8 significant
+  bits relative to its (site, s) maximum.
+* The block operator and the block preconditioner are checked element by
+  element: every (site, s) against its own maximum (bounds derived at BTOL).
 """
 import numpy as np
 import pytest
@@ -33,6 +33,18 @@ def dwf():
 
 def relerr(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def elem_relerr(got, want):
+    """Largest, over the (s, site) elements of a canonical half field, of
+    max|got - want| / max|want| with both maxima over that element's own 24
+    reals: every element is held to the tolerance relative to its own size."""
+    g = np.stack([got.real, got.imag], -1)
+    w = np.stack([want.real, want.imag], -1)
+    num = np.abs(g - w).max(axis=(-3, -2, -1))
+    den = np.abs(w).max(axis=(-3, -2, -1))
+    assert (den > 0).all()
+    return float((num / den).max())
 
 
 class Setup:
@@ -164,7 +176,15 @@ def test_mdagm_hermitian_positive_fp64():
 # ----------------------------------------------------------------------------
 # block operator and preconditioner
 # ----------------------------------------------------------------------------
-BTOL = {"fp32": 1e-5, "fp16": 5e-3, "bf16": 4e-2}
+# Element-wise bounds (each (site, s) against its own maximum). FP32 storage:
+# a few hundred FP32 roundings along the four-hop chain, 1e-5. FP16 / BF16
+# storage: four stored intermediates, each rounded to 2^-11 / 2^-8 of its own
+# (site, s) maximum, so about 4 * 2^-11 = 2e-3 (FP16) and 1.6e-2 (BF16) of the
+# terms that meet in one output element; an output element may be a few times
+# smaller than those terms (partial cancellation of the M_5 and hop parts), so
+# the bounds are 1e-2 and 8e-2. Any indexing or region error is O(1) and the
+# FP32 case resolves errors down to 1e-5.
+BTOL = {"fp32": 1e-5, "fp16": 1e-2, "bf16": 8e-2}
 
 
 @pytest.mark.parametrize("dims,block", [((8, 4, 6, 4), (2, 2, 2, 4)), ((4, 8, 4, 8), (4, 2, 2, 4)),
@@ -189,7 +209,7 @@ def test_block_apply(dims, block, inner, snake):
             f = sv.a_block if snake else sv.a_block_truncated
             want += f(S.act, S.U, sv.project(x, m), masses[r], m)
         want = op.full_to_half(want, 0)
-        err = np.linalg.norm(got[r] - want) / np.linalg.norm(want)
+        err = elem_relerr(got[r], want)
         assert err < BTOL[inner], (r, err)
 
 
@@ -207,9 +227,58 @@ def test_block_precond(inner, k):
     got = S.from_native(z, "fp32", 1)[0]
     want = op.full_to_half(sv.ms_precondition(S.act, S.U, op.half_to_full(r_in[0], 0), masses[0],
                                               block, k, form="definition"), 0)
-    err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    # k CG steps amplify storage rounding mildly
-    assert err < (1e-5 * k if inner == "fp32" else 2e-2), err
+    err = elem_relerr(got, want)
+    # k CG steps with block scalars formed from reductions over the whole
+    # block: an element's error is set by the block's scale, not its own, so
+    # the bound is wider than the operator's (FP32: 1e-5 per step; FP16:
+    # 5e-2)
+    assert err < (1e-5 * k if inner == "fp32" else 5e-2), err
+
+
+@pytest.fixture(scope="module")
+def production_blocks():
+    """16^4 x Ls=12 lattice cut into the 8^3 x 16 blocks of the benchmark
+    workload (8 blocks), so that every block's distance-1 and distance-2 rings
+    and its per-block links have their production size. The oracle's box form
+    of A_s (pinned against the definition on small lattices) gives A_s x on two
+    of the blocks, and 2 inner CG steps on one of them."""
+    S = Setup((16, 16, 16, 16), 12, eps=0.4, seed=1005)
+    block, mf, k = (8, 8, 8, 16), 0.01, 2
+    src = S.source(2005)
+    x = op.half_to_full(src, 0)
+    origins = sv.block_origins(S.act.dims, block)
+    even = op.parity_mask(S.act.shape4) == 0
+    want = {}
+    for o in (origins[0], origins[-1]):
+        m = sv.block_mask(S.act, block, o)
+        want[o] = (m & even, sv.a_block_box(S.act, S.U, sv.project(x, m), mf, o, block))
+    o = origins[-1]
+    m = sv.block_mask(S.act, block, o)
+    z = sv.cg_fixed(lambda v: sv.a_block_box(S.act, S.U, v, mf, o, block), sv.project(x, m), k)
+    return S, block, mf, k, src, want, (m & even, z)
+
+
+@pytest.mark.parametrize("inner", ["fp32", "fp16"])
+def test_block_apply_production_shape(production_blocks, inner):
+    S, block, mf, k, src, want, _ = production_blocks
+    prm = dwf().default_params(block=block, inner=inner)
+    out = S.ctx.new_field("fp32", 1)
+    S.ctx.block_apply(out, S.to_native([src], "fp32"), prm, [mf])
+    got = op.half_to_full(S.from_native(out, "fp32", 1)[0], 0)
+    for o, (sel, w) in want.items():
+        err = elem_relerr(got[:, sel], w[:, sel])
+        assert err < BTOL[inner], (o, err)
+
+
+@pytest.mark.parametrize("inner", ["fp32", "fp16"])
+def test_block_precond_production_shape(production_blocks, inner):
+    S, block, mf, k, src, _, (sel, zwant) = production_blocks
+    prm = dwf().default_params(block=block, inner=inner, inner_iters=k)
+    z = S.ctx.new_field("fp32", 1)
+    S.ctx.block_precond(z, S.to_native([src], "fp32"), prm, [mf])
+    got = op.half_to_full(S.from_native(z, "fp32", 1)[0], 0)
+    err = elem_relerr(got[:, sel], zwant[:, sel])
+    assert err < (1e-5 * k if inner == "fp32" else 5e-2), err
 
 
 def test_dslash_full_size_sampled():
@@ -280,7 +349,7 @@ def test_mdagm_and_block_apply_recon12():
                 m = sv.block_mask(S.act, block, o)
                 want += sv.a_block(S.act, S.U, sv.project(x, m), masses[r], m)
             want = op.full_to_half(want, 0)
-            err = np.linalg.norm(got[r] - want) / np.linalg.norm(want)
+            err = elem_relerr(got[r], want)
             assert err < BTOL[inner], (inner, r, err)
 
 

@@ -79,9 +79,9 @@ def test_solve_counts_block_operator_hops_and_keeps_the_solution():
     # block operator: hops 3 and 4 are the FP16 adjoint with its epilogue, two
     # per inner iteration; each preconditioner application runs k of them
     k = 4
-    blk_dag = stats["hop2_kernel<F16,1,0,0,1>"]["launches"]
-    blk_pre = stats["hop2_kernel<F16,0,1,0,1>"]["launches"]
-    blk_mid = stats["hop2_kernel<F16,0,0,0,1>"]["launches"]
+    blk_dag = stats["hop2_kernel<F16,1,0,0,1> [block]"]["launches"]
+    blk_pre = stats["hop2_kernel<F16,0,1,0,1> [block]"]["launches"]
+    blk_mid = stats["hop2_kernel<F16,0,0,0,1> [block]"]["launches"]
     assert blk_dag == 2 * blk_pre == 2 * blk_mid
     assert blk_pre % k == 0 and blk_pre // k >= info1[0]["outer_iters"]
     # outer operator in FP32, reliable updates in FP64
@@ -89,6 +89,28 @@ def test_solve_counts_block_operator_hops_and_keeps_the_solution():
     assert any(n.startswith("hop_kernel<F64") for n in stats)
     total = sum(s["seconds"] for s in stats.values())
     assert 0 < total < info1[0]["seconds"]
+    # dslash_gbs: the outer operator's FP32 hops of this solve (timer on)
+    outer = [s for n, s in stats.items() if n.startswith("hop2_kernel<F32") and "[block]" not in n]
+    gbs = sum(s["alg_bytes"] for s in outer) / sum(s["seconds"] for s in outer) / 1e9
+    assert info1[0]["dslash_gbs"] > 0
+    assert abs(info1[0]["dslash_gbs"] - gbs) < 1e-6 * gbs
+    assert info0[0]["dslash_gbs"] == -1.0  # timer off
+
+
+def test_block_operator_with_fp32_storage_has_its_own_slots():
+    """With FP32 inner storage the block operator runs the same kernel
+    instantiations as the outer FP32 operator; its launches are counted apart
+    (" [block]"), so dslash_gbs covers the outer operator only."""
+    dwf, ctx, canon = setup()
+    prm = dwf.default_params(block=(4, 4, 4, 8), inner="fp32", inner_iters=2, tol=1e-10)
+    ctx.profile(True)
+    st, info = ctx.solve(torch.zeros_like(canon), canon, [MF], prm)
+    stats = by_name(ctx.profile_read())
+    ctx.profile(False)
+    assert st == 0
+    assert stats["hop2_kernel<F32,1,0,0,1> [block]"]["launches"] % 2 == 0
+    assert stats["hop2_kernel<F32,1,0,0,1>"]["launches"] >= 2 * info[0]["outer_iters"]
+    assert info[0]["dslash_gbs"] > 0
 
 
 def test_profile_read_argument_errors():

@@ -142,6 +142,74 @@ def test_inner_cg_many_iterations_is_exact(small_block):
 
 
 # ----------------------------------------------------------------------------
+# The multisplitting preconditioner M^-1 = (+)_s CG_k(A_s) (Sec. 2.4): the
+# assembly over several blocks against a dense block-diagonal construction
+# ----------------------------------------------------------------------------
+def krylov_optimal(A, r, k):
+    """The A-norm-optimal approximation of A^-1 r in K_k(A, r), computed densely
+    (Galerkin projection on an orthonormal Krylov basis), which is what k CG
+    steps from a zero guess produce in exact arithmetic."""
+    V = [r]
+    for _ in range(k - 1):
+        V.append(A @ V[-1])
+    Q, _ = np.linalg.qr(np.array(V).T)
+    return Q @ np.linalg.solve(Q.conj().T @ A @ Q, Q.conj().T @ r)
+
+
+@pytest.fixture(scope="module")
+def four_blocks():
+    """4x4x2x2 x Ls=2 lattice cut into 2^4 blocks: two blocks in x and two in y,
+    one block (keeping its periodic wrap) in z and t. Dense A = D_PC^+ D_PC on
+    all even sites, from the oracle's pinned operator."""
+    act = op.Action(dims=(4, 4, 2, 2), Ls=2, **MOB)
+    U = gauge(act, seed=21)
+    mf = 0.07
+    A, idx = dense_on(lambda v: op.mdagm(act, U, v, mf), act, np.ones(act.shape4, bool))
+    block = (2, 2, 2, 2)
+    sels = []
+    for o in sv.block_origins(act.dims, block):
+        m = sv.block_mask(act, block, o)
+        m5 = np.broadcast_to(m[None, :, :, :, :, None, None], act.shape5).reshape(-1)
+        sels.append((o, m, np.flatnonzero(m5[idx])))
+    r = rand_even(act)
+    return act, U, mf, A, idx, block, sels, r
+
+
+def test_block_partition_covers_even_sites_once(four_blocks):
+    act, U, mf, A, idx, block, sels, r = four_blocks
+    assert len(sels) == 4
+    allsel = np.concatenate([s for _, _, s in sels])
+    assert np.array_equal(np.sort(allsel), np.arange(len(idx)))
+
+
+@pytest.mark.parametrize("form", ["definition", "box"])
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_ms_precondition_is_block_diagonal_stack(four_blocks, form, k):
+    """z = M^-1 r equals, on every block s, the Krylov-optimal k-step solution
+    of the dense sub-matrix A[s, s] (= P_s A P_s, Sec. 2.3) with the block's
+    part of r; the blocks do not couple."""
+    act, U, mf, A, idx, block, sels, r = four_blocks
+    z = sv.ms_precondition(act, U, r, mf, block, k, form=form).reshape(-1)[idx]
+    rv = r.reshape(-1)[idx]
+    for origin, _, sel in sels:
+        want = krylov_optimal(A[np.ix_(sel, sel)], rv[sel], k)
+        assert np.abs(z[sel] - want).max() < 1e-12 * np.abs(want).max(), origin
+
+
+def test_ms_precondition_truncated_is_block_diagonal_stack(four_blocks):
+    """The same stacking with the snake-truncated block operator (snake = 0),
+    whose dense form comes block by block from a_block_truncated."""
+    act, U, mf, A, idx, block, sels, r = four_blocks
+    k = 3
+    z = sv.ms_precondition(act, U, r, mf, block, k, snake=False)
+    for origin, mask, _ in sels:
+        At, bidx = dense_on(lambda v, m=mask: sv.a_block_truncated(act, U, v, mf, m), act, mask)
+        want = krylov_optimal(At, r.reshape(-1)[bidx], k)
+        got = z.reshape(-1)[bidx]
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), origin
+
+
+# ----------------------------------------------------------------------------
 # MSPCG (Algorithm 1 with the multisplitting preconditioner)
 # ----------------------------------------------------------------------------
 def test_mspcg_solves_and_matches_dense():

@@ -55,3 +55,17 @@ def test_noalloc_refuses_fields_beyond_its_scratch():
         ctx.mdagm_noalloc(g, f, "fp32", [0.1])
     assert e.value.code == 1 and "DWF_NOALLOC_SCRATCH_BYTES" in str(e.value)
     ctx.close()
+
+
+def test_noalloc_rejects_a_nan_mass():
+    """Like dwf_mdagm, the no-allocation variant refuses a NaN quark mass."""
+    from paper_1811_08488_gb300 import dwf
+    dims, Ls = (4, 4, 4, 4), 4
+    ctx = dwf.Context(dims, Ls)
+    ctx.gauge_load(syn.gauge_field(dims, 0.4, 8))
+    f, g = ctx.new_field("fp32"), ctx.new_field("fp32")
+    for fn in (ctx.mdagm, ctx.mdagm_noalloc):
+        with pytest.raises(dwf.DwfError) as e:
+            fn(g, f, "fp32", [float("nan")])
+        assert e.value.code == 1 and "NaN" in str(e.value)
+    ctx.close()
