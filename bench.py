@@ -1,11 +1,14 @@
 """Benchmark: MSPCG vs plain CG time-to-solve at residual 1e-10 on one GB300,
 and the hop (Dslash) kernel's HBM bandwidth.
 
-Workload (default): Moebius DWF 16^3 x 32 x Ls=12, b=1.5, c=0.5, M5=1.8,
-m_f=0.01, SU(3) links exp(i 0.4 H) (seed 1001), one Gaussian source (seed
-2001 + rank). MSPCG: 8^3 x 16 blocks (16 blocks), 6 inner CG iterations in
+Headline workload: Moebius DWF 24^3 x 64 x Ls=16, b=1.5, c=0.5, M5=1.8,
+m_f=0.003, SU(3) links exp(i 0.45 H) (seed 1002), one Gaussian source (seed
+2002 + rank). MSPCG: 12^3 x 16 blocks (32 blocks), 6 inner CG iterations in
 FP16 storage, FP32 outer iterations with FP64 reductions and reliable updates.
-Plain CG: the same outer solver without the preconditioner.
+Plain CG: the same outer solver without the preconditioner. This is the
+largest workload whose solves fit the benchmark's step count in a few minutes
+(one MSPCG solve of the 32^3 x 64 x 12 workload with 4 right-hand sides takes
+about a minute); that workload is measured once per solver as an extra key.
 
 A step is one full MSPCG solve (every stage of the path) to a true residual
 of 1e-10. `value` is the mean MSPCG time-to-solution over the timed steps.
@@ -16,13 +19,17 @@ Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 and source; the timed region is bracketed by barriers and the maximum over
 ranks is reported ("replicas only": the path has no data exchange on one GPU).
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (see cpu_sample()).
+workload (see reference_sample()).
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
+import hashlib
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -35,13 +42,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MSPCG vs plain CG time-to-solve at resid 1e-10 (1 GB300); Dslash HBM GB/s"
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the hop kernels
-# inside the MSPCG solve of this workload, from one ncu capture of the same
-# bench command on the current kernels (see profiles/); a kernel missing here
-# reports traffic null. hop2_kernel<F16,1,0,0,1>: block-operator hops 4 and 3,
-# (185.43 + 26.95) and (174.87 + 49.17) MB, mean of the two launches.
-DRAM_BYTES_PER_LAUNCH = {"hop2_kernel<F16,1,0,0,1>": 218210560}
-WORKLOAD = "mobius_16^3x32x12"
+WORKLOAD = "mobius_24^3x64x16"          # headline
+LARGE = "mobius_32^3x64x12_4rhs"        # extra key: one timed solve per solver
+SMALL = "mobius_16^3x32x12"             # extra key: the 16^3 x 32 x 12 solves
+MULTI = "mobius_16^3x32x12_16rhs"       # tensor-core M_5^-1 with 16 right-hand sides
+INNER_K = 6
+
+# Outer iterations of the GB300 MSPCG solve of the headline workload (k = 6,
+# 12^3 x 16 blocks), recorded from the GB300 arm. The reference arm cannot
+# solve the workload (hours of CPU time), so it scales its sample by this
+# count and says so; the GB300 arm's own cpu_baseline uses the count it
+# measured in the same run.
+MSPCG_OUTER_ITERS_RECORDED = 193
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
+# of the timed MSPCG solves, from one ncu capture of the headline workload;
+# valid only while the hop kernel sources hash to `source_sha` (otherwise the
+# line reports traffic null).
+KNOWN_TRAFFIC = {}
+HOP_SOURCES = ["paper_1811_08488_gb300/csrc/hop.cu", "paper_1811_08488_gb300/csrc/device_common.cuh",
+               "paper_1811_08488_gb300/csrc/dwf_internal.cuh"]
+
+
+def hop_source_sha() -> str:
+    h = hashlib.sha256()
+    for p in HOP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -50,6 +78,12 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def nsites5(name):
+    from paper_1811_08488_gb300 import synthetic as syn
+    w = syn.WORKLOADS[name]
+    return int(np.prod(w["dims"])) // 2 * w["Ls"]
 
 
 # ----------------------------------------------------------------------------
@@ -107,49 +141,146 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle sample (cpu_baseline and --impl reference)
+# CPU oracle: measured timings (cpu_baseline) and the reference arm's sample
 # ----------------------------------------------------------------------------
-def cpu_sample(outer_iters, k, nblocks):
-    """Time one application of the oracle's block operator A_s on one
-    8^3 x 16 block of the workload (the cut-out box form, FP64 numpy) and
-    scale it to a full MSPCG solve: the oracle's cost is proportional to the
-    sites it sweeps, so A on the whole lattice costs t_As * V / V_box, and
-    one outer iteration costs A + k * nblocks * A_s."""
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_inputs(name):
+    from oracle import dwf_operator as op
+    from paper_1811_08488_gb300 import synthetic as syn
+    w = syn.WORKLOADS[name]
+    act = op.Action(dims=w["dims"], Ls=w["Ls"], M5=w["M5"], b=w["b"], c=w["c"])
+    Uc = syn.gauge_field(w["dims"], w["eps"], 1000 + w["id"])
+    src = syn.half_field(w["dims"], w["Ls"], 2000 + w["id"])
+    return w, act, Uc, src
+
+
+def oracle_block_inputs(name):
+    from oracle import dwf_operator as op
+    w, act, Uc, src = _oracle_inputs(name)
+    return w, act, op.gauge_to_mu_major(Uc), op.half_to_full(src, 0)
+
+
+def oracle_block_sample(name, block, inputs=None):
+    """Seconds of one oracle A_s application (the box form, FP64 numpy) on the
+    block at the origin of workload `name`, and the 5D sites of its box."""
+    from oracle import solvers as sv
+    w, act, U, x = inputs or oracle_block_inputs(name)
+    mask = sv.block_mask(act, block, (0, 0, 0, 0))
+    t0 = time.perf_counter()
+    sv.a_block_box(act, U, sv.project(x, mask), w["mf"][0], (0, 0, 0, 0), block)
+    t = time.perf_counter() - t0
+    box = int(np.prod([sv.box_extent(L, b) for L, b in zip(w["dims"], block)])) // 2 * w["Ls"]
+    return t, box
+
+
+def oracle_one_core_jobs():
+    """The oracle's single-core measurements (run in a worker process while the
+    GPU part of the benchmark runs; numpy's arithmetic here is single-threaded):
+    * a full FP64 plain-CG solve of the Shamir 8^4 x 8 workload to 1e-10;
+    * one A = D_PC^+ D_PC application on the 16^3 x 32 x 12 lattice;
+    * one A_s application on a 6^3 x 8 block box of the headline workload."""
+    import threadpoolctl
     from oracle import dwf_operator as op
     from oracle import solvers as sv
-    from paper_1811_08488_gb300 import synthetic as syn
-    w = syn.WORKLOADS[WORKLOAD]
-    act = op.Action(dims=w["dims"], Ls=w["Ls"], M5=w["M5"], b=w["b"], c=w["c"])
-    U = op.gauge_to_mu_major(syn.gauge_field(w["dims"], w["eps"], 1000 + w["id"]))
-    b = op.half_to_full(syn.half_field(w["dims"], w["Ls"], 2000 + w["id"]), 0)
-    block, origin = w["block"], (0, 0, 0, 0)
-    mask = sv.block_mask(act, block, origin)
+    out = {}
+    with threadpoolctl.threadpool_limits(1):
+        w, act, Uc, src = _oracle_inputs("shamir_8^4x8")
+        U = op.gauge_to_mu_major(Uc)
+        b = op.half_to_full(src, 0)
+        t0 = time.perf_counter()
+        _, it, res = sv.cg(lambda v: op.mdagm(act, U, v, w["mf"][0]), b, 1e-10)
+        out["c1_plain_cg"] = {"seconds": time.perf_counter() - t0, "iters": it, "true_resid": res}
+        w, act, Uc, src = _oracle_inputs(SMALL)
+        U = op.gauge_to_mu_major(Uc)
+        x = op.half_to_full(src, 0)
+        t0 = time.perf_counter()
+        op.mdagm(act, U, x, w["mf"][0])
+        out["c2_A"] = {"seconds": time.perf_counter() - t0, "sites5": nsites5(SMALL)}
+        t, box = oracle_block_sample(WORKLOAD, (6, 6, 6, 8))
+        out["headline_As_box"] = {"seconds": t, "sites5": box, "block": "6^3x8"}
+    return out
+
+
+def oracle_all_cores_A():
+    """One A application on the 16^3 x 32 x 12 lattice with every host core:
+    the oracle evaluates A in time slabs in worker processes (oracle/slabs.py)."""
+    from oracle import dwf_operator as op
+    from oracle import slabs
+    w, act, Uc, src = _oracle_inputs(SMALL)
+    n = os.cpu_count() or 1
     t0 = time.perf_counter()
-    sv.a_block_box(act, U, sv.project(b, mask), w["mf"][0], origin, block)
-    t_as = time.perf_counter() - t0
-    vbox = np.prod([min(L, bl + 4) for L, bl in zip(w["dims"], block)])
-    t_a = t_as * np.prod(w["dims"]) / vbox
-    per_outer = t_a + k * nblocks * t_as
-    return {"value": float(outer_iters * per_outer), "t_sample": t_as,
-            "sample": (f"one FP64 oracle A_s apply on one 8^3x16 block box ({t_as:.1f} s), "
-                       f"scaled to {outer_iters} outer iterations x (A + {k} x {nblocks} A_s)")}
+    slabs.mdagm_half(act, Uc, src, w["mf"][0], slab=4, workers=n)
+    return {"seconds": time.perf_counter() - t0, "cores": n}
 
 
-def cpu_sample_1core(outer_iters, k, nblocks):
-    """cpu_sample() with every numpy/BLAS thread pool limited to one thread
-    (the oracle's arrays ops are single-threaded numpy): returns (sample, cores)."""
-    try:
-        import threadpoolctl
-        with threadpoolctl.threadpool_limits(1):
-            return cpu_sample(outer_iters, k, nblocks), 1
-    except ImportError:
-        return cpu_sample(outer_iters, k, nblocks), 1
+def extrapolate(t_site_A, t_site_As, name, block, outer_iters, k=INNER_K):
+    """Oracle seconds of one solve of `name`: per outer iteration one A on the
+    lattice plus k A_s on every block's box, each scaled from a measured
+    per-5D-site cost."""
+    from oracle import solvers as sv
+    from paper_1811_08488_gb300 import synthetic as syn
+    w = syn.WORKLOADS[name]
+    nblocks = int(np.prod([d // b for d, b in zip(w["dims"], block)]))
+    box = int(np.prod([sv.box_extent(L, b) for L, b in zip(w["dims"], block)])) // 2 * w["Ls"]
+    per_outer = t_site_A * nsites5(name) + k * nblocks * t_site_As * box
+    return outer_iters * per_outer, per_outer
 
 
-# Outer iterations of the GB300 MSPCG solve of this workload (measured by the
-# GB300 arm: 118 at k = 6, 8^3 x 16 blocks). The reference arm scales its
-# per-iteration sample by it, since a full FP64 oracle solve takes hours.
-MSPCG_OUTER_ITERS = 118
+def cpu_baseline(one_core, all_cores, outer_ms, outer_plain):
+    """The oracle as it stands on this host's cores (measured), and the
+    headline solve extrapolated from those measurements by the GPU arm's
+    iteration counts of this run."""
+    from paper_1811_08488_gb300 import synthetic as syn
+    block = syn.WORKLOADS[WORKLOAD]["block"]
+    t_A = one_core["c2_A"]["seconds"] / one_core["c2_A"]["sites5"]
+    t_As = one_core["headline_As_box"]["seconds"] / one_core["headline_As_box"]["sites5"]
+    ms, _ = extrapolate(t_A, t_As, WORKLOAD, block, outer_ms)
+    plain = outer_plain * t_A * nsites5(WORKLOAD)
+    return {"value": round(ms, 1), "unit": "s", "cores": 1, "kind": "oracle",
+            "value_is": "extrapolated: measured per-site oracle costs x the GB300 arm's outer "
+                        "iterations of this run",
+            "sample": (f"measured on 1 core: one A on 16^3x32x12 ({one_core['c2_A']['seconds']:.1f} s), "
+                       f"one A_s on a 6^3x8 block box of {WORKLOAD} "
+                       f"({one_core['headline_As_box']['seconds']:.1f} s); scaled per 5D site to "
+                       f"{outer_ms} MSPCG outer iterations x (A + {INNER_K} x nblocks x A_s on "
+                       f"12^3x16 block boxes)"),
+            "plain_cg_extrapolated_s": round(plain, 1),
+            "measured": {
+                "shamir_8^4x8_plain_cg_fp64": {
+                    "1_core": {"seconds": round(one_core["c1_plain_cg"]["seconds"], 2),
+                               "iters": one_core["c1_plain_cg"]["iters"],
+                               "true_resid": one_core["c1_plain_cg"]["true_resid"]},
+                    "all_cores": "same as 1 core: the oracle's numpy arithmetic is single-threaded"},
+                "A_16^3x32x12": {"1_core_s": round(one_core["c2_A"]["seconds"], 2),
+                                 "all_cores_s": round(all_cores["seconds"], 2) if all_cores else None,
+                                 "all_cores": all_cores["cores"] if all_cores else None},
+                "A_s_6^3x8_box_of_headline": {"1_core_s": round(one_core["headline_As_box"]["seconds"], 2)},
+            },
+            "host": {"nproc": os.cpu_count(), "cpu": cpu_model(), "machine": platform.machine()}}
+
+
+def reference_sample(inputs):
+    """One step of the reference arm: one oracle A_s application on a 6^3 x 8
+    block box of the headline workload on one core (measured), scaled per 5D
+    site to the headline MSPCG solve with the recorded GB300 outer-iteration
+    count. `inputs` (oracle_block_inputs) are drawn once, outside the steps."""
+    import threadpoolctl
+    with threadpoolctl.threadpool_limits(1):
+        t, box = oracle_block_sample(WORKLOAD, (6, 6, 6, 8), inputs)
+    from paper_1811_08488_gb300 import synthetic as syn
+    block = syn.WORKLOADS[WORKLOAD]["block"]
+    per_site = t / box
+    total, per_outer = extrapolate(per_site, per_site, WORKLOAD, block, MSPCG_OUTER_ITERS_RECORDED)
+    return t, total
 
 
 # ----------------------------------------------------------------------------
@@ -176,11 +307,11 @@ def bench_config(world):
     from paper_1811_08488_gb300 import synthetic as syn
     w = syn.WORKLOADS[WORKLOAD]
     nblocks = int(np.prod([d // bl for d, bl in zip(w["dims"], w["block"])]))
-    return {"workload": WORKLOAD, "lattice": "16^3x32", "Ls": w["Ls"], "b": w["b"], "c": w["c"],
-            "M5": w["M5"], "mf": w["mf"][0], "gauge_eps": w["eps"], "block": "8^3x16",
-            "nblocks": nblocks, "inner_iters": 6, "inner": "fp16+scale", "outer": "fp32",
+    return {"workload": WORKLOAD, "lattice": "24^3x64", "Ls": w["Ls"], "b": w["b"], "c": w["c"],
+            "M5": w["M5"], "mf": w["mf"][0], "gauge_eps": w["eps"], "block": "12^3x16",
+            "nblocks": nblocks, "inner_iters": INNER_K, "inner": "fp16+scale", "outer": "fp32",
             "reductions": "fp64", "tol": 1e-10, "parallelism": f"replicas{world}",
-            "l2": "solve working set > L2 (about 1.3 GB); 256 MB L2 flush between steps"}
+            "l2": "solve working set > L2 (about 10 GB); 256 MB L2 flush between steps"}
 
 
 def flush_l2(buf):
@@ -189,225 +320,162 @@ def flush_l2(buf):
     buf.sum()
 
 
+class Timer:
+    def __init__(self, stream, flush):
+        self.stream, self.flush = stream, flush
+
+    def call(self, fn, reps=20, warm=3):
+        """Median device time of fn() (CUDA events on the launching stream, L2
+        flushed before each repetition)."""
+        import torch
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush_l2(self.flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts)
+
+    def solves(self, ctx, x, b, masses, prm, n, dist=None):
+        """n solves, each bracketed by (barrier +) synchronize and CUDA events."""
+        import torch
+        out = []
+        for _ in range(n):
+            flush_l2(self.flush)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            st, info = ctx.solve(x, b, masses, prm)
+            e1.record(self.stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            out.append((e0.elapsed_time(e1) * 1e-3, st, info))
+        return out
+
+
+def dslash_line(ctx, T, canon, mf, prec, dagger, nrhs=1):
+    """One hop launch (dwf_dslash_eo, even output) on native fields of `prec`:
+    device time, compulsory bytes (every input and output element once, the
+    links of both parities once) and their ratio."""
+    fin, fout = ctx.new_field(prec, nrhs), ctx.new_field(prec, nrhs)
+    ctx.field_import(fin, prec, canon, nrhs)
+    V4 = int(np.prod(ctx.dims))
+    eb = {"fp32": 96, "fp16": 52, "bf16": 52, "fp64": 192}[prec]
+    lb = {"fp32": 72, "fp16": 36, "bf16": 36, "fp64": 144}[prec]
+    alg = 2 * (V4 // 2) * ctx.Ls * eb * nrhs + V4 * 4 * lb
+    masses = [mf] * nrhs
+    t = T.call(lambda: ctx.dslash_eo(fout, fin, 0, dagger, prec, masses))
+    peak, kind = peaks()
+    del fin, fout
+    return {"us": round(t * 1e6, 2), "alg_bytes": alg, "gbs": round(alg / t / 1e9, 1),
+            "frac": round(alg / t / 1e9 / peak, 4), "frac_of_8tbs_nominal": round(alg / t / 8e12, 4)}
+
+
+def kernel_table(kstats, t_steps):
+    rows = []
+    for k in sorted(kstats, key=lambda d: -d["seconds"]):
+        rows.append({"kernel": k["name"], "launches": k["launches"], "ms": round(k["seconds"] * 1e3, 3),
+                     "share": round(k["seconds"] / t_steps, 4),
+                     "avg_us": round(k["seconds"] / k["launches"] * 1e6, 2),
+                     "gbs": round(k["alg_bytes"] / k["seconds"] / 1e9, 1)})
+    return rows
+
+
 def run_gpu(args, rank, world, dist):
     import torch
     from paper_1811_08488_gb300 import dwf, synthetic as syn
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    T = Timer(stream, torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda"))  # 256 MB
+    peak, peak_kind = peaks()
+    res = {}
+
+    # --- headline workload ------------------------------------------------------
     w = syn.WORKLOADS[WORKLOAD]
     dims, Ls, mf = w["dims"], w["Ls"], w["mf"][0]
     Uc = syn.gauge_field(dims, w["eps"], 1000 + w["id"])
     src = syn.half_field(dims, Ls, replica_source_seed(w["id"], rank))
     ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"], device=dev)
     ctx.gauge_load(Uc)
-    stream = torch.cuda.current_stream()
-    V4 = int(np.prod(dims))
-    Vh = V4 // 2
-    l2_flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
-
-    # --- hop kernel bandwidth (FP32, the solver's outer launch shape) ---------
-    canon = torch.from_numpy(src[None].copy()).cuda()
-    fin = ctx.new_field("fp32")
-    fout = ctx.new_field("fp32")
-    ctx.field_import(fin, "fp32", canon)
-    alg_bytes = 2 * Vh * Ls * 24 * 4 + V4 * 4 * 18 * 4
-    for _ in range(5):
-        ctx.dslash_eo(fout, fin, 0, 0, "fp32", [mf])
-    times = []
-    for _ in range(30):
-        flush_l2(l2_flush)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.dslash_eo(fout, fin, 0, 0, "fp32", [mf])
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) * 1e-3)
-    t_hop = statistics.median(times)
-    hop_gbs = alg_bytes / t_hop / 1e9
-
-    # the same kernel on FP16 fields (the storage of the inner block solves,
-    # which take most of the MSPCG time): 48 B + 4 B scale per (site, s),
-    # 36 B FP16 links
-    f16in = ctx.new_field("fp16")
-    f16out = ctx.new_field("fp16")
-    ctx.field_import(f16in, "fp16", canon)
-    alg16 = 2 * Vh * Ls * (48 + 4) + V4 * 4 * 18 * 2
-    for _ in range(5):
-        ctx.dslash_eo(f16out, f16in, 0, 1, "fp16", [mf])
-    times16 = []
-    for _ in range(30):
-        flush_l2(l2_flush)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.dslash_eo(f16out, f16in, 0, 1, "fp16", [mf])
-        e1.record(stream)
-        e1.synchronize()
-        times16.append(e0.elapsed_time(e1) * 1e-3)
-    t_hop16 = statistics.median(times16)
-
-    def time_call(fn, reps=10):
-        for _ in range(3):
-            fn()
-        ts = []
-        for _ in range(reps):
-            flush_l2(l2_flush)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1) * 1e-3)
-        return statistics.median(ts)
-
-    # --- M_5^-1 on the tensor cores, 16 right-hand sides (the multi-RHS shape) ---
-    m5 = None
-    if not args.dslash_only:
-        nr = args.m5_rhs
-        m16 = list(syn.log_spaced_masses(0.001, 0.05, nr))
-        canon16 = canon.expand(nr, *canon.shape[1:]).contiguous()
-        peak_m5, _ = peaks()
-        m5 = {"nrhs": nr, "note": "call time: kernel + 4-byte status read + stream sync"}
-        for prec, bpe in (("fp32", 96), ("fp16", 52)):
-            fi, fo = ctx.new_field(prec, nr), ctx.new_field(prec, nr)
-            ctx.field_import(fi, prec, canon16, nr)
-            t = time_call(lambda: ctx.m5inv_gemm(fo, fi, 0, prec, m16))
-            alg = 2 * Vh * Ls * bpe * nr
-            m5[prec] = {"us": round(t * 1e6, 1), "alg_bytes": alg, "gbs": round(alg / t / 1e9, 1),
-                        "frac": round(alg / t / 1e9 / peak_m5, 4)}
-            if prec == "fp32":
-                t_cc = time_call(lambda: ctx.m5inv(fo, fi, 0, "fp32", m16))
-                m5["closed_form_fp32"] = {"kernel": "ls_kernel (CUDA cores)",
-                                          "us": round(t_cc * 1e6, 1),
-                                          "gbs": round(alg / t_cc / 1e9, 1)}
-            del fi, fo
-        del canon16
-        torch.cuda.empty_cache()
-        if args.m5_only:
-            return {"metric": "M_5^-1 GEMM HBM GB/s", "m5inv_gemm": m5,
-                    "config": {"workload": WORKLOAD, "nrhs": nr}}, None, None
-
-    if args.dslash_only:
-        times_dag = []
-        for _ in range(30):
-            flush_l2(l2_flush)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.dslash_eo(fout, fin, 0, 1, "fp32", [mf])
-            e1.record(stream)
-            e1.synchronize()
-            times_dag.append(e0.elapsed_time(e1) * 1e-3)
-        t_dag = statistics.median(times_dag)
-        peak, kind = peaks()
-        res = {"metric": "Dslash HBM GB/s", "value": round(hop_gbs, 1), "unit": "GB/s",
-               "higher_is_better": True, "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
-               "dagger_us": round(t_dag * 1e6, 2), "dagger_gbs": round(alg_bytes / t_dag / 1e9, 1),
-               "frac": round(hop_gbs / peak, 4), "config": {"workload": WORKLOAD}}
-        if args.dslash_fp64:
-            # the FP64 hop of the reliable updates (after the FP32 and FP16 launches)
-            d_in, d_out = ctx.new_field("fp64"), ctx.new_field("fp64")
-            ctx.field_import(d_in, "fp64", canon)
-            t64 = time_call(lambda: ctx.dslash_eo(d_out, d_in, 0, 0, "fp64", [mf]), 5)
-            res["fp64_us"] = round(t64 * 1e6, 1)
-        return res, None, None
-
-    # --- solves -----------------------------------------------------------------
-    b = canon
+    del Uc
+    b = torch.from_numpy(src[None]).cuda()
     x = torch.zeros_like(b)
-    p_ms = dwf.default_params(inner_iters=6, block=w["block"], inner="fp16", outer="fp32",
+
+    # the hop kernel on this lattice (fields ~10x L2): the "Dslash HBM GB/s"
+    dsl = dslash_line(ctx, T, b, mf, "fp32", 0)
+    dsl["kernel"] = "hop2_kernel<F32,0,1,0,0> (M^4 = -1/2 Dhop M_phi, M_phi on load)"
+    dsl_dag = dslash_line(ctx, T, b, mf, "fp32", 1)
+    dsl16 = dslash_line(ctx, T, b, mf, "fp16", 1)
+
+    p_ms = dwf.default_params(inner_iters=INNER_K, block=w["block"], inner="fp16", outer="fp32",
                               tol=1e-10)
     p_plain = dwf.default_params(inner_iters=0, outer="fp32", tol=1e-10)
-
-    def timed_solves(prm, n, collect):
-        out = []
-        for _ in range(n):
-            flush_l2(l2_flush)
-            if dist:
-                dist.barrier()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, info = ctx.solve(x, b, [mf], prm)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            if collect:
-                out.append((e0.elapsed_time(e1) * 1e-3, st, info[0]))
-        return out
-
-    timed_solves(p_plain, max(1, args.warmup // 2), False)
-    plain = timed_solves(p_plain, max(1, args.steps // 2 + 1), True)
+    T.solves(ctx, x, b, [mf], p_plain, max(1, args.warmup // 2), dist)
+    plain = T.solves(ctx, x, b, [mf], p_plain, max(1, args.steps // 2 + 1), dist)
     # the hop-kernel timer runs inside the timed MSPCG solves: its graphs are
     # captured with the timer during the warm-up, and the counters are reset
     # right before the timed region
     ctx.profile(True)
-    timed_solves(p_ms, args.warmup, False)
+    T.solves(ctx, x, b, [mf], p_ms, args.warmup, dist)
     ctx.profile(True)
     with ClockSampler(dev) as clk:
-        ms = timed_solves(p_ms, args.steps, True)
+        ms = T.solves(ctx, x, b, [mf], p_ms, args.steps, dist)
     kstats = ctx.profile_read()
     ctx.profile(False)
-    # the same solves without the timer (its cost, for the record)
-    timed_solves(p_ms, 1, False)
-    ms_off = timed_solves(p_ms, max(1, args.steps // 2 + 1), True)
-    # the block autotuner's shape for this workload (the configured 8^3 x 16
-    # blocks stay the benchmark value): tuning cost and the solve with it
-    p_auto = dwf.default_params(inner_iters=6, block=(0, 0, 0, 0), inner="fp16", outer="fp32",
-                                tol=1e-10)
-    t0 = time.perf_counter()
-    blk_auto, _ = ctx.autotune_block(b, [mf], p_auto, trial=20)
-    t_tune = time.perf_counter() - t0
-    timed_solves(p_auto, 1, False)
-    auto = timed_solves(p_auto, max(1, args.steps // 2 + 1), True)
-    if dist:
-        auto_t = max_over_ranks([statistics.mean(t for t, _, _ in auto)], dist, "cuda")[0]
-    else:
-        auto_t = statistics.mean(t for t, _, _ in auto)
-    mspcg_auto = {"block": "x".join(map(str, blk_auto)), "seconds": round(auto_t, 6),
-                  "outer_iters": auto[-1][2]["outer_iters"], "tuning_seconds": round(t_tune, 3),
-                  "converged": all(st == 0 and i["converged"] for _, st, i in auto)}
+    ms_off = T.solves(ctx, x, b, [mf], p_ms, 1, dist)
 
-    # e2e: host buffers, copies inside the timed region
-    bh = torch.from_numpy(src[None].copy()).pin_memory()
+    # e2e: host buffers, copies inside the timed region (the solve copies b in
+    # and x out through mspcg_solve's io_on_host path)
+    bh = torch.from_numpy(src[None]).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
-    p_e2e = dwf.default_params(inner_iters=6, block=w["block"], inner="fp16", outer="fp32",
+    p_e2e = dwf.default_params(inner_iters=INNER_K, block=w["block"], inner="fp16", outer="fp32",
                                tol=1e-10, io_on_host=1)
     ctx.solve(xh, bh, [mf], p_e2e)
     e2e_t = []
-    for _ in range(args.steps):
-        flush_l2(l2_flush)
+    for _ in range(max(1, min(args.steps, 3))):
+        flush_l2(T.flush)
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, info = ctx.solve(xh, bh, [mf], p_e2e)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
+    h2d, d2h = int(bh.numel() * 16), int(xh.numel() * 16)
+    del bh, xh, b, x
+    ctx.close()
+    torch.cuda.empty_cache()
 
     t_ms = statistics.mean(t for t, _, _ in ms)
     t_plain = statistics.mean(t for t, _, _ in plain)
     t_e2e = statistics.mean(e2e_t)
     if dist:
         t_ms, t_plain, t_e2e = max_over_ranks([t_ms, t_plain, t_e2e], dist, "cuda")
-    info_ms, info_plain = ms[-1][2], plain[-1][2]
-    ok = all(st == 0 and i["converged"] for _, st, i in ms + plain)
-    k = 6
-    nblocks = int(np.prod([d // bl for d, bl in zip(dims, w["block"])]))
-    launches_ms = (1 + 1 + (6 * k + 1) + 2 + info_ms["outer_iters"] * (6 + 6 * k + 1)
-                   + info_ms["reliable_updates"] * (6 + 6 * k + 2) + 1)
-    peak, kind = peaks()
-    # the dominant kernel of the timed solves, from the hop-kernel timer:
-    # achieved = its compulsory bytes / its device time, summed over launches
+    info_ms, info_plain = ms[-1][2][0], plain[-1][2][0]
+    ok = all(st == 0 and i[0]["converged"] for _, st, i in ms + plain)
     t_steps = sum(t for t, _, _ in ms)
-    kernels = []
-    for kst in sorted(kstats, key=lambda d: -d["seconds"]):
-        kernels.append({"kernel": kst["name"], "launches": kst["launches"],
-                        "ms": round(kst["seconds"] * 1e3, 3),
-                        "share": round(kst["seconds"] / t_steps, 4),
-                        "avg_us": round(kst["seconds"] / kst["launches"] * 1e6, 2),
-                        "gbs": round(kst["alg_bytes"] / kst["seconds"] / 1e9, 1)})
     dom = max(kstats, key=lambda d: d["seconds"])
     dom_gbs = dom["alg_bytes"] / dom["seconds"] / 1e9
-    dom_traffic = DRAM_BYTES_PER_LAUNCH.get(dom["name"])
-    res = {
+    known = KNOWN_TRAFFIC.get(dom["name"])
+    sha = hop_source_sha()
+    dom_traffic = known["bytes"] if known and known["source_sha"] == sha else None
+    nblocks = int(np.prod([d // bl for d, bl in zip(dims, w["block"])]))
+    hop_launches = sum(k["launches"] for k in kstats)
+    # BLAS / gather / scatter launches per outer iteration besides the hops:
+    # outer axpy_xr, xpay_p; inner gather, scatter, k x (xr) + (k - 1) x p
+    blas_per_iter = 2 + 2 + INNER_K + (INNER_K - 1)
+    launches = hop_launches + args.steps * (info_ms["outer_iters"] * blas_per_iter +
+                                            info_ms["reliable_updates"] * (4 + blas_per_iter) + 8)
+    res.update({
         "metric": METRIC,
         "value": round(t_ms, 6),
         "unit": "s",
@@ -422,42 +490,132 @@ def run_gpu(args, rank, world, dist):
         "data": "synthetic",
         "config": bench_config(world),
         "mspcg": {"seconds": round(t_ms, 6),
-                  "seconds_without_kernel_timer": round(statistics.mean(t for t, _, _ in ms_off), 6),
+                  "seconds_without_kernel_timer": round(ms_off[0][0], 6),
                   "outer_iters": info_ms["outer_iters"],
                   "inner_iters_total": info_ms["inner_iters_total"],
                   "reliable_updates": info_ms["reliable_updates"],
-                  "true_resid": info_ms["true_resid"]},
+                  "true_resid": info_ms["true_resid"],
+                  "dslash_gbs": round(info_ms["dslash_gbs"], 1)},
         "plain_cg": {"seconds": round(t_plain, 6), "outer_iters": info_plain["outer_iters"],
                      "reliable_updates": info_plain["reliable_updates"],
                      "true_resid": info_plain["true_resid"]},
         "mspcg_speedup_vs_plain": round(t_plain / t_ms, 4),
-        "mspcg_autotuned": mspcg_auto,
         "all_converged": ok,
-        "dslash": {"kernel": "hop2_kernel<F32,DAG=0,PRE=1> (M^4 = -1/2 Dhop M_phi)",
-                   "us": round(t_hop * 1e6, 2), "alg_bytes": alg_bytes,
-                   "gbs": round(hop_gbs, 1), "frac_of_8tbs_nominal": round(hop_gbs / 8000, 4)},
-        "m5inv_gemm": m5,
-        "dslash_fp16_dagger": {"kernel": "hop2_kernel<F16,DAG=1,PRE=0>", "us": round(t_hop16 * 1e6, 2),
-                               "alg_bytes": alg16, "gbs": round(alg16 / t_hop16 / 1e9, 1),
-                               "frac": round(alg16 / t_hop16 / 1e9 / peak, 4)},
+        "dslash": dsl,
+        "dslash_fp32_dagger": dsl_dag,
+        "dslash_fp16_dagger": dsl16,
         # the dominant kernel of the timed MSPCG solves (hop-kernel timer):
         # achieved = compulsory bytes / device time over all its launches in
-        # the timed region; traffic = dram read + write per launch from one
-        # ncu capture of the same bench command (profiles/), null if none
+        # the timed region; traffic = dram read + write per launch from one ncu
+        # capture of this workload on the same kernel sources, else null
         "roofline": {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(dom_gbs / peak, 4), "traffic": dom_traffic,
                      "frac_of_8tbs_nominal": round(dom_gbs / 8000, 4),
-                     "kernel": dom["name"], "peak_kind": kind, "launches": dom["launches"],
+                     "kernel": dom["name"], "peak_kind": peak_kind, "launches": dom["launches"],
                      "share_of_timed_solves": round(dom["seconds"] / t_steps, 4),
                      "avg_launch_us": round(dom["seconds"] / dom["launches"] * 1e6, 2),
-                     "alg_bytes_per_launch": int(dom["alg_bytes"] / dom["launches"])},
-        "hop_kernels_in_timed_solves": kernels,
-        "e2e": {"value": round(t_e2e, 6), "unit": "s",
-                "h2d_bytes_per_step": int(bh.numel() * 16), "d2h_bytes_per_step": int(xh.numel() * 16)},
-        "gpu_launches": int(launches_ms),
+                     "alg_bytes_per_launch": int(dom["alg_bytes"] / dom["launches"]),
+                     "hop_source_sha": sha},
+        "hop_kernels_in_timed_solves": kernel_table(kstats, t_steps),
+        "e2e": {"value": round(t_e2e, 6), "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
         "clocks": clk.summary(),
-    }
-    return res, info_ms, nblocks
+    })
+
+    if not args.headline_only:
+        res["small"] = run_small(args, T, rank, dist)
+        if not args.no_large:
+            res["large"] = run_large(args, T, rank, dist)
+    return res, info_ms, info_plain
+
+
+def run_small(args, T, rank, dist):
+    """The 16^3 x 32 x 12 workload: MSPCG (configured and autotuned blocks) and
+    plain CG, and the tensor-core M_5^-1 with 16 right-hand sides."""
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    w = syn.WORKLOADS[SMALL]
+    dims, Ls, mf = w["dims"], w["Ls"], w["mf"][0]
+    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"],
+                      device=int(os.environ.get("LOCAL_RANK", 0)))
+    ctx.gauge_load(syn.gauge_field(dims, w["eps"], 1000 + w["id"]))
+    b = torch.from_numpy(syn.half_field(dims, Ls, replica_source_seed(w["id"], rank))[None]).cuda()
+    x = torch.zeros_like(b)
+    out = {"workload": SMALL, "dslash": dslash_line(ctx, T, b, mf, "fp32", 0)}
+    for name, prm in (("plain_cg", dwf.default_params(inner_iters=0, tol=1e-10)),
+                      ("mspcg", dwf.default_params(inner_iters=INNER_K, block=w["block"], tol=1e-10))):
+        T.solves(ctx, x, b, [mf], prm, 1, dist)
+        r = T.solves(ctx, x, b, [mf], prm, 3, dist)
+        out[name] = {"seconds": round(statistics.mean(t for t, _, _ in r), 6),
+                     "outer_iters": r[-1][2][0]["outer_iters"],
+                     "converged": all(st == 0 and i[0]["converged"] for _, st, i in r)}
+    p_auto = dwf.default_params(inner_iters=INNER_K, block=(0, 0, 0, 0), tol=1e-10)
+    t0 = time.perf_counter()
+    blk, _ = ctx.autotune_block(b, [mf], p_auto, trial=20)
+    t_tune = time.perf_counter() - t0
+    T.solves(ctx, x, b, [mf], p_auto, 1, dist)
+    r = T.solves(ctx, x, b, [mf], p_auto, 3, dist)
+    out["mspcg_autotuned"] = {"block": "x".join(map(str, blk)), "tuning_seconds": round(t_tune, 3),
+                              "seconds": round(statistics.mean(t for t, _, _ in r), 6),
+                              "outer_iters": r[-1][2][0]["outer_iters"],
+                              "converged": all(st == 0 and i[0]["converged"] for _, st, i in r)}
+    # tensor-core M_5^-1, 16 right-hand sides of log-spaced masses (one call)
+    wm = syn.WORKLOADS[MULTI]
+    nr = len(wm["mf"])
+    canon16 = b.expand(nr, *b.shape[1:]).contiguous()
+    peak, _ = peaks()
+    m5 = {"nrhs": nr, "note": "call time: kernel + 4-byte status read + stream sync"}
+    Vh = int(np.prod(dims)) // 2
+    for prec, bpe in (("fp32", 96), ("fp16", 52)):
+        fi, fo = ctx.new_field(prec, nr), ctx.new_field(prec, nr)
+        ctx.field_import(fi, prec, canon16, nr)
+        t = T.call(lambda: ctx.m5inv_gemm(fo, fi, 0, prec, list(wm["mf"])), reps=10)
+        alg = 2 * Vh * Ls * bpe * nr
+        m5[prec] = {"us": round(t * 1e6, 1), "alg_bytes": alg, "gbs": round(alg / t / 1e9, 1),
+                    "frac": round(alg / t / 1e9 / peak, 4)}
+        if prec == "fp32":
+            t_cc = T.call(lambda: ctx.m5inv(fo, fi, 0, "fp32", list(wm["mf"])), reps=10)
+            m5["closed_form_fp32"] = {"kernel": "ls_kernel (CUDA cores)", "us": round(t_cc * 1e6, 1),
+                                      "gbs": round(alg / t_cc / 1e9, 1)}
+        del fi, fo
+    out["m5inv_gemm_16rhs"] = m5
+    del canon16, b, x
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_large(args, T, rank, dist):
+    """The 32^3 x 64 x 12 workload with 4 right-hand sides (m_f 0.0008): the
+    hop kernel on fields ~20x L2, and one timed solve per solver (all four
+    right-hand sides in one call) after an untimed two-iteration solve that
+    builds the plans and graphs."""
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    w = syn.WORKLOADS[LARGE]
+    dims, Ls, masses = w["dims"], w["Ls"], list(w["mf"])
+    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"],
+                      device=int(os.environ.get("LOCAL_RANK", 0)))
+    ctx.gauge_load(syn.gauge_field(dims, w["eps"], 1000 + w["id"]))
+    srcs = [syn.half_field(dims, Ls, replica_source_seed(w["id"], rank) + r) for r in range(len(masses))]
+    b = torch.from_numpy(np.stack(srcs)).cuda()
+    del srcs
+    x = torch.zeros_like(b)
+    out = {"workload": LARGE, "dslash": dslash_line(ctx, T, b[:1], masses[0], "fp32", 0)}
+    for name, kw in (("plain_cg", dict(inner_iters=0)),
+                     ("mspcg", dict(inner_iters=INNER_K, block=w["block"]))):
+        T.solves(ctx, x, b, masses, dwf.default_params(tol=1e-10, maxiter=2, **kw), 1, dist)
+        r = T.solves(ctx, x, b, masses, dwf.default_params(tol=1e-10, **kw), 1, dist)
+        t, st, info = r[0]
+        out[name] = {"seconds": round(t, 4), "outer_iters": [i["outer_iters"] for i in info],
+                     "true_resid": [float(f"{i['true_resid']:.3e}") for i in info],
+                     "converged": st == 0 and all(i["converged"] for i in info)}
+    out["mspcg_speedup_vs_plain"] = round(out["plain_cg"]["seconds"] / out["mspcg"]["seconds"], 4)
+    del b, x
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -649,17 +807,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dslash-only", action="store_true",
-                    help="time only the FP32 hop kernel (used for kernel profiles)")
-    ap.add_argument("--dslash-fp64", action="store_true",
-                    help="with --dslash-only: also time the FP64 hop")
-    ap.add_argument("--m5-only", action="store_true",
-                    help="time only the tensor-core M_5^-1 (used for kernel profiles)")
-    ap.add_argument("--m5-rhs", type=int, default=16, help="right-hand sides of the M_5^-1 timing")
-    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta", "resident",
-                             "flexible"],
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline workload (no 16^3x32 and 32^3x64 extra keys)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64x12 extra key")
+    ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta",
+                                        "resident", "flexible"],
                     help="solver parameter sweep instead of the benchmark line")
-    ap.add_argument("--workload", default=WORKLOAD, help="workload of --study")
+    ap.add_argument("--workload", default=SMALL, help="workload of --study")
     ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")
     ap.add_argument("--recon12", action="store_true", help="--study with reconstruct-12 links")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold of --study")
@@ -673,27 +827,39 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        from paper_1811_08488_gb300 import synthetic as syn
-        w = syn.WORKLOADS[WORKLOAD]
-        # iteration count of the GB300 MSPCG solve of this workload (measured),
-        # used to scale the per-iteration sample
-        nblocks = 16
-        vals = []
+        steps, vals = [], []
+        inputs = oracle_block_inputs(WORKLOAD)
         for i in range(args.warmup + args.steps):
-            s, cores = cpu_sample_1core(MSPCG_OUTER_ITERS, 6, nblocks)
+            t, v = reference_sample(inputs)
             if i >= args.warmup:
-                vals.append(s["value"])
+                steps.append(t)
+                vals.append(v)
         v = statistics.mean(vals)
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+        nb = bench_config(1)["nblocks"]
+        sample = (f"per step: one FP64 oracle A_s application on a 6^3x8 block box of {WORKLOAD} on "
+                  f"1 core ({statistics.mean(steps):.1f} s, measured), scaled per 5D site to one MSPCG "
+                  f"solve: {MSPCG_OUTER_ITERS_RECORDED} outer iterations (the GB300 arm's recorded "
+                  f"count) x (A + {INNER_K} x {nb} A_s on 12^3x16 block boxes)")
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "s",
+                          "value_is": "extrapolated from the measured sample (ms_per_step is the "
+                                      "sample's own time)",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                          "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
-                          "scaling": "weak", "vs_baseline": None, "data": "synthetic", "dtype": "f64",
-                          "config": bench_config(args.gpus),
-                          "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": cores,
-                                           "kind": "oracle", "sample": s["sample"]},
-                          "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                          "ms_per_step": round(statistics.mean(steps) * 1e3, 1),
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                          "data": "synthetic", "dtype": "f64", "config": bench_config(args.gpus),
+                          "cpu_baseline": {"value": round(v, 1), "unit": "s", "cores": 1,
+                                           "kind": "oracle", "sample": sample},
+                          "e2e": {"value": round(v, 1), "unit": "s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
         return
+
+    # the oracle's single-core measurements run in a worker process (started
+    # with "spawn" before the first GPU call) while the GPU part runs
+    pool, fut = None, None
+    want_cpu = world == 1 and not args.no_cpu_baseline
+    if want_cpu:
+        pool = cf.ProcessPoolExecutor(1, mp_context=mp.get_context("spawn"))
+        fut = pool.submit(oracle_one_core_jobs)
 
     dist = None
     if world > 1:
@@ -705,12 +871,14 @@ def main():
         # or reduction with an error after this long instead of the default 10 min
         td.init_process_group("nccl", timeout=datetime.timedelta(seconds=300))
         dist = td
-    res, info_ms, nblocks = run_gpu(args, rank, world, dist)
+    res, info_ms, info_plain = run_gpu(args, rank, world, dist)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and not args.dslash_only and not args.m5_only:
-            s, cores = cpu_sample_1core(info_ms["outer_iters"], 6, nblocks)
-            res["cpu_baseline"] = {"value": round(s["value"], 3), "unit": "s",
-                                   "cores": cores, "kind": "oracle", "sample": s["sample"]}
+        if want_cpu:
+            one = fut.result()
+            pool.shutdown()
+            all_c = oracle_all_cores_A()
+            res["cpu_baseline"] = cpu_baseline(one, all_c, info_ms["outer_iters"],
+                                               info_plain["outer_iters"])
         print(json.dumps(res))
     if dist:
         dist.barrier()

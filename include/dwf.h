@@ -114,10 +114,16 @@ typedef struct {
   dwf_prec inner;     /* DWF_FP32, DWF_FP16 or DWF_BF16 block-solve storage     */
   double delta;       /* reliable update when |r| < delta * max|r| since last   */
   int snake;          /* 1: A_s = P_s A P_s (snake terms), 0: per-hop Dirichlet */
-  int use_graph;      /* 1: replay the iteration from a captured CUDA graph     */
+  int use_graph;      /* 1: the outer loop runs on the device as one CUDA graph 
+                       * (a while-node over the iteration; after every      
+                       * iteration a control kernel decides each rhs's       
+                       * reliable update and convergence); the host waits   
+                       * once per 256 iterations. 0: the host drives the     
+                       * loop with eager launches, checking every            
+                       * check_every iterations.                             */
   int io_on_host;     /* mspcg_solve: 1 = x and b are host pointers             */
-  int check_every;    /* outer iterations between host convergence checks,    
-                       * 1 .. 256                                             */
+  int check_every;    /* host-driven loop (use_graph 0): outer iterations      
+                       * between host convergence checks, 1 .. 256            */
   int flexible;       /* 1: flexible PCG, beta = <r_new - r, z_new> / <r, z>    
                        * (Polak-Ribiere); 0: Algorithm 1's <r_new, z_new> /   
                        * <r, z> (Fletcher-Reeves)                             */
@@ -136,6 +142,9 @@ typedef struct {
                           * call, over their device time (GB/s; same for all
                           * rhs), from the hop-kernel timer; -1 when the     
                           * timer is off (dwf_profile_enable)               */
+  int host_syncs;        /* host waits for the device in the outer loop     */
+  int device_loop;       /* 1: convergence and reliable updates were decided
+                          * on the device (use_graph), 0: by the host       */
 } dwf_solve_info;
 
 /* Device time of one hop-kernel family, from dwf_profile_read. */
@@ -319,9 +328,13 @@ dwf_status dwf_autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const doubl
  * even half fields (device pointers, or host pointers when params->io_on_host).
  * Outer iterations run in params->outer precision with FP64 reductions; with
  * FP32 outer precision the residual is recomputed in FP64 (reliable update)
- * whenever |r| fell by params->delta, and at convergence. `info` (host array
- * of nrhs) is filled on success and on NOT_CONVERGED. Synchronous: returns
- * when x is written. Errors: INVALID_ARG, NO_GAUGE, NOT_CONVERGED, NAN, CUDA. */
+ * whenever |r| fell by params->delta, and at convergence. All right-hand
+ * sides iterate in the same launches; each stops on its own when its
+ * reliable update confirms |b - A x| <= tol |b| (with use_graph the device
+ * decides this after every iteration and skips the finished right-hand sides
+ * in every later kernel). `info` (host array of nrhs) is filled on success and
+ * on NOT_CONVERGED. Synchronous: returns when x is written.
+ * Errors: INVALID_ARG, NO_GAUGE, NOT_CONVERGED, NAN, CUDA. */
 dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs,
                        const double *mf, const dwf_solver_params *params,
                        dwf_solve_info *info, void *stream);

@@ -20,6 +20,8 @@ solvers       CG, fixed-k inner CG, the Dirichlet block operator A_s with and
               without snake terms, and Algorithm 1 with the multisplitting
               preconditioner (paper Sec. 2.1, 2.3, 2.4, Algorithm 1).
 pointwise     the hop at one (site, s), for spot checks on large lattices.
+slabs         A = D_PC^dag D_PC on large lattices, evaluated in time slabs
+              by worker processes (A couples sites at most four apart).
 
 Parity status: every function is pinned by a CPU test against a closed form,
 an invariant, a dense brute-force computation or a library routine (see

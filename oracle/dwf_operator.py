@@ -270,10 +270,47 @@ def mdagm(act: Action, U, psi_e, mf: float) -> np.ndarray:
     return mpc(act, U, mpc(act, U, psi_e, mf, False), mf, True)
 
 
+def mpc_sym(act: Action, U, psi_e, mf: float, dagger: bool = False) -> np.ndarray:
+    """The symmetric Schur form D_sym = 1 - M_5^-1 M^4_eo M_5^-1 M^4_oe on even
+    fields, the even-odd reduction with the diagonal block divided out (a
+    variant of the paper's D_PC of eq. (dirac_equation); D_PC psi_e = phi_hat_e
+    and D_sym psi_e = M_5^-1 phi_hat_e have the same solution). The adjoint is
+    1 - (M^4_oe)^dag M_5^-dag (M^4_eo)^dag M_5^-dag."""
+    if not dagger:
+        t = restrict_parity(m4(act, U, psi_e, mf), 1)
+        t = m5inv(act, t, mf)
+        t = restrict_parity(m4(act, U, t, mf), 0)
+        return psi_e - m5inv(act, t, mf)
+    t = m5inv(act, psi_e, mf, True)
+    t = restrict_parity(m4(act, U, t, mf, True), 1)
+    t = m5inv(act, t, mf, True)
+    t = restrict_parity(m4(act, U, t, mf, True), 0)
+    return psi_e - t
+
+
+def mdagm_sym(act: Action, U, psi_e, mf: float) -> np.ndarray:
+    """A_sym = D_sym^dag D_sym, the normal operator of the symmetric form."""
+    return mpc_sym(act, U, mpc_sym(act, U, psi_e, mf, False), mf, True)
+
+
+def normal_op(schur: str):
+    """The normal operator of a Schur form: "asym" (the paper's D_PC) or "sym"."""
+    return {"asym": mdagm, "sym": mdagm_sym}[schur]
+
+
 def source_prep(act: Action, U, phi_e, phi_o, mf: float) -> np.ndarray:
     """phi_hat_e = phi_e - M^4_eo M_5^-1 phi_o (paper eq. (dirac_equation))."""
     t = m5inv(act, phi_o, mf)
     return phi_e - restrict_parity(m4(act, U, t, mf), 0)
+
+
+def normal_source(act: Action, U, phi_e, phi_o, mf: float, schur: str = "asym") -> np.ndarray:
+    """Right-hand side of the normal equation of a Schur form for D psi = phi:
+    D_PC^dag phi_hat_e, or D_sym^dag M_5^-1 phi_hat_e for the symmetric form."""
+    ph = source_prep(act, U, phi_e, phi_o, mf)
+    if schur == "asym":
+        return mpc(act, U, ph, mf, True)
+    return mpc_sym(act, U, m5inv(act, ph, mf), mf, True)
 
 
 def odd_reconstruct(act: Action, U, psi_e, phi_o, mf: float) -> np.ndarray:

@@ -87,6 +87,29 @@ def cg_fixed(apply_A, r, k: int):
     return z
 
 
+def cg_stop(apply_A, r, kmax: int, eps: float):
+    """CG on A z = r from z = 0 that stops at the first iteration whose
+    recursively updated residual satisfies |r_k| <= eps |r|, or after kmax
+    iterations (the inner solve with a residual stop instead of a fixed k, a
+    variant the paper's Sec. 4 invites). Returns (z, iterations)."""
+    z = np.zeros_like(r)
+    res = r.copy()
+    p = res.copy()
+    rr = op.norm2(res)
+    stop = eps * eps * rr
+    k = 0
+    while k < kmax and rr > stop and rr > 0.0:
+        Ap = apply_A(p)
+        alpha = rr / op.vdot(p, Ap).real
+        z = z + alpha * p
+        res = res - alpha * Ap
+        rr_new = op.norm2(res)
+        p = res + (rr_new / rr) * p
+        rr = rr_new
+        k += 1
+    return z, k
+
+
 def pcg(apply_A, apply_Minv, b, tol: float, maxiter: int = 100000):
     """Algorithm 1: preconditioned CG on A x = b, x_0 = 0.
 
@@ -149,13 +172,14 @@ def project(psi: np.ndarray, mask4: np.ndarray) -> np.ndarray:
     return psi * mask4[None, :, :, :, :, None, None]
 
 
-def a_block(act: op.Action, U, x, mf: float, mask4) -> np.ndarray:
+def a_block(act: op.Action, U, x, mf: float, mask4, schur: str = "asym") -> np.ndarray:
     """A_s x = P_s D_PC^dag D_PC P_s x on the full lattice (snake terms kept).
 
     This is the definition of Sec. 2.3: Dirichlet conditions on the whole
     normal operator, so every path that leaves the block and comes back
-    contributes."""
-    return project(op.mdagm(act, U, project(x, mask4), mf), mask4)
+    contributes. schur="sym": the same with the symmetric form's normal
+    operator."""
+    return project(op.normal_op(schur)(act, U, project(x, mask4), mf), mask4)
 
 
 def a_block_truncated(act: op.Action, U, x, mf: float, mask4) -> np.ndarray:
@@ -205,7 +229,7 @@ def extract_box(act: op.Action, U, origin, block):
     return box, Ub, coords
 
 
-def a_block_box(act: op.Action, U, x, mf: float, origin, block) -> np.ndarray:
+def a_block_box(act: op.Action, U, x, mf: float, origin, block, schur: str = "asym") -> np.ndarray:
     """A_s x computed on the cut-out box; equal to a_block (pinned by a test).
 
     The box origin is chosen so that box parity equals lattice parity (all
@@ -216,7 +240,7 @@ def a_block_box(act: op.Action, U, x, mf: float, origin, block) -> np.ndarray:
     t, z, y, xx = np.indices(box.shape4)
     for coord, c_lat, o, bl in zip((xx, y, z, t), (bx, by, bz, bt), origin, block):
         inb &= (c_lat[coord] >= o) & (c_lat[coord] < o + bl)
-    yb = project(op.mdagm(box, Ub, project(xb, inb), mf), inb)
+    yb = project(op.normal_op(schur)(box, Ub, project(xb, inb), mf), inb)
     out = np.zeros_like(x)
     T, Z, Y, X = np.meshgrid(bt, bz, by, bx, indexing="ij")
     out[:, T[inb], Z[inb], Y[inb], X[inb]] = yb[:, inb]
@@ -227,26 +251,33 @@ def a_block_box(act: op.Action, U, x, mf: float, origin, block) -> np.ndarray:
 # Multisplitting preconditioner and MSPCG
 # ----------------------------------------------------------------------------
 def ms_precondition(act: op.Action, U, r, mf: float, block, k: int,
-                    snake: bool = True, form: str = "box") -> np.ndarray:
+                    snake: bool = True, form: str = "box", inner_tol: float = 0.0,
+                    schur: str = "asym") -> np.ndarray:
     """z = M^-1 r with M = (+)_s A_s (Sec. 2.4): on every block, k CG iterations
     on A_s z_s = r_s from a zero guess, with block-local scalars; no coupling
-    between blocks."""
+    between blocks. inner_tol > 0: each block stops early once its residual
+    fell by inner_tol (cg_stop, at most k iterations)."""
     z = np.zeros_like(r)
     for origin in block_origins(act.dims, block):
         mask = block_mask(act, block, origin)
         if not snake:
             A = lambda v, m=mask: a_block_truncated(act, U, v, mf, m)
         elif form == "box":
-            A = lambda v, o=origin: a_block_box(act, U, v, mf, o, block)
+            A = lambda v, o=origin: a_block_box(act, U, v, mf, o, block, schur)
         else:
-            A = lambda v, m=mask: a_block(act, U, v, mf, m)
-        z += project(cg_fixed(A, project(r, mask), k), mask)
+            A = lambda v, m=mask: a_block(act, U, v, mf, m, schur)
+        rs = project(r, mask)
+        zs = cg_stop(A, rs, k, inner_tol)[0] if inner_tol > 0 else cg_fixed(A, rs, k)
+        z += project(zs, mask)
     return z
 
 
 def mspcg(act: op.Action, U, b, mf: float, block, k: int, tol: float,
-          maxiter: int = 100000, snake: bool = True):
-    """MSPCG: Algorithm 1 with the multisplitting preconditioner."""
-    A = lambda v: op.mdagm(act, U, v, mf)
-    Minv = lambda v: ms_precondition(act, U, v, mf, block, k, snake)
+          maxiter: int = 100000, snake: bool = True, inner_tol: float = 0.0,
+          schur: str = "asym"):
+    """MSPCG: Algorithm 1 with the multisplitting preconditioner, on the normal
+    equation of the paper's D_PC (schur="asym") or of the symmetric form."""
+    A = lambda v: op.normal_op(schur)(act, U, v, mf)
+    Minv = lambda v: ms_precondition(act, U, v, mf, block, k, snake, inner_tol=inner_tol,
+                                     schur=schur)
     return pcg(A, Minv, b, tol, maxiter)

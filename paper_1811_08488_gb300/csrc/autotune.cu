@@ -41,14 +41,8 @@ std::vector<std::array<int, 4>> block_candidates(const int dims[4]) {
 
 // Destroy every cached outer-iteration graph (they hold block-plan pointers).
 static void drop_graphs(dwf_ctx *ctx) {
-  for (auto &kv : ctx->solver_plans) {
-    SolverPlan *sp = kv.second.get();
-    if (sp && sp->graph) {
-      cudaGraphExecDestroy(sp->graph);
-      sp->graph = nullptr;
-      sp->graph_key.clear();
-    }
-  }
+  for (auto &kv : ctx->solver_plans)
+    if (kv.second) kv.second->drop_graphs();
 }
 
 static std::string plan_key(const int block[4], dwf_prec inner) {

@@ -253,6 +253,111 @@ __global__ void set_rz_kernel(OuterScalars *scal, const int *skip, int nrhs) {
   if (r < nrhs && !(skip && skip[r])) scal[r].rz = scal[r].rz_new;
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven loop of the outer solve: one thread decides, after every outer
+// iteration, which right-hand sides take a reliable update and whether the
+// graph's loop goes on; the decisions are the host loop's (the same tests on
+// the same FP64 scalars), taken without a host round trip.
+// ---------------------------------------------------------------------------
+// Before the first iteration: |r| = |b|; a zero source is solved by x = 0.
+__global__ void solve_start_kernel(OuterScalars *scal, SolveCtl *ctl, int *skip_iter,
+                                   SolveCtl init) {
+  if (threadIdx.x != 0) return;
+  *ctl = init;
+  for (int r = 0; r < init.nrhs; ++r) {
+    OuterScalars &s = scal[r];
+    s.maxr = sqrt(s.rr);
+    s.done = s.bb == 0.0 ? 1 : 0;
+    s.final_res = s.done ? 0.0 : -1.0;
+    s.nru = 0;
+    skip_iter[r] = s.done;
+  }
+}
+
+// At the start of every graph launch.
+__global__ void solve_launch_kernel(SolveCtl *ctl) {
+  if (threadIdx.x == 0) {
+    ctl->launch_iters = 0;
+  }
+}
+
+// After an outer iteration: a right-hand side takes a reliable update when its
+// iterated |r|^2 reached tol^2 |b|^2 (convergence candidate) or |r| fell below
+// delta times its largest value since the last update.
+__global__ void solve_control_kernel(OuterScalars *scal, SolveCtl *ctl, int *skip_ru,
+                                     cudaGraphConditionalHandle h_loop,
+                                     cudaGraphConditionalHandle h_ru) {
+  if (threadIdx.x != 0) return;
+  int any_ru = 0, iter_max = 0;
+  for (int r = 0; r < ctl->nrhs; ++r) {
+    OuterScalars &s = scal[r];
+    skip_ru[r] = 1;
+    if (s.done) continue;
+    const double rr = s.rr;
+    if (!isfinite(rr)) {
+      ctl->nan = 1;
+      continue;
+    }
+    const double nr = sqrt(rr);
+    const bool need = rr <= ctl->tol2 * s.bb || nr < ctl->delta * s.maxr;
+    s.maxr = fmax(s.maxr, nr);
+    if (need) {
+      skip_ru[r] = 0;
+      any_ru = 1;
+    }
+    iter_max = max(iter_max, s.iter);
+  }
+  ctl->launch_iters += 1;
+  const bool stop = ctl->nan || ctl->launch_iters >= ctl->budget || iter_max >= ctl->maxiter;
+  cudaGraphSetConditional(h_ru, (any_ru && !ctl->nan) ? 1u : 0u);
+  cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+}
+
+// After a reliable update: the recomputed FP64 |b - A x|^2 is in rr; a right-
+// hand side whose true residual meets tol is done and skipped from now on.
+__global__ void solve_post_ru_kernel(OuterScalars *scal, SolveCtl *ctl, const int *skip_ru,
+                                     int *skip_iter, cudaGraphConditionalHandle h_loop) {
+  if (threadIdx.x != 0) return;
+  int open = 0;
+  for (int r = 0; r < ctl->nrhs; ++r) {
+    OuterScalars &s = scal[r];
+    if (!s.done && !skip_ru[r]) {
+      s.nru += 1;
+      const double rr = s.rr;
+      if (!isfinite(rr)) ctl->nan = 1;
+      s.maxr = sqrt(rr);
+      if (rr <= ctl->tol2 * s.bb) {
+        s.done = 1;
+        skip_iter[r] = 1;
+        s.final_res = sqrt(rr / s.bb);
+      }
+    }
+    open += !s.done;
+  }
+  if (open == 0 || ctl->nan) cudaGraphSetConditional(h_loop, 0u);
+}
+
+void solve_start(OuterScalars *scal, SolveCtl *ctl, int *skip_iter, const SolveCtl &init,
+                 cudaStream_t st) {
+  solve_start_kernel<<<1, 32, 0, st>>>(scal, ctl, skip_iter, init);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+void solve_launch(SolveCtl *ctl, cudaStream_t st) {
+  solve_launch_kernel<<<1, 32, 0, st>>>(ctl);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+void solve_control(OuterScalars *scal, SolveCtl *ctl, int *skip_ru,
+                   cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_ru,
+                   cudaStream_t st) {
+  solve_control_kernel<<<1, 32, 0, st>>>(scal, ctl, skip_ru, h_loop, h_ru);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+void solve_post_ru(OuterScalars *scal, SolveCtl *ctl, const int *skip_ru, int *skip_iter,
+                   cudaGraphConditionalHandle h_loop, cudaStream_t st) {
+  solve_post_ru_kernel<<<1, 32, 0, st>>>(scal, ctl, skip_ru, skip_iter, h_loop);
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
 #define DISPATCH_LO(lo, KERNEL, ...)                                        \
   do {                                                                      \
     dim3 g(kOuterCtas, nrhs);                                               \

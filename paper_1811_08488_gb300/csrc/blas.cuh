@@ -55,6 +55,16 @@ void outer_copy_p(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
 void outer_promote(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
 void outer_ru_residual(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);
 void outer_set_rz(const OuterArgs &A, int nrhs, cudaStream_t st);
+
+// Device-driven outer loop (see blas.cu).
+void solve_start(OuterScalars *scal, SolveCtl *ctl, int *skip_iter, const SolveCtl &init,
+                 cudaStream_t st);
+void solve_launch(SolveCtl *ctl, cudaStream_t st);
+void solve_control(OuterScalars *scal, SolveCtl *ctl, int *skip_ru,
+                   cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_ru,
+                   cudaStream_t st);
+void solve_post_ru(OuterScalars *scal, SolveCtl *ctl, const int *skip_ru, int *skip_iter,
+                   cudaGraphConditionalHandle h_loop, cudaStream_t st);
 int outer_ctas();
 
 void block_gather(dwf_prec in, const BlockArgs &B, int nrhs, cudaStream_t st);

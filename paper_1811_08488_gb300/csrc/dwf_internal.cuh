@@ -239,8 +239,24 @@ struct OuterScalars {
   double apz;     // <A p, z_{k+1}> (flexible PCG)
   double bb;      // |b|^2
   int iter;       // iterations done
+  int done;       // converged: a reliable update confirmed |b - A x| <= tol |b|
+  double maxr;    // largest |r| since the last reliable update
+  double final_res;  // |b - A x| / |b| once done (-1 while open)
+  int nru;        // reliable updates done
   int pad;
   double hist_rr[kHistory];
+};
+
+// Loop state of the device-driven outer solve (one per solve): the device
+// decides the reliable updates and convergence after every iteration and ends
+// the graph's loop when every right-hand side is done, on a NaN, at maxiter,
+// or after `budget` iterations of one graph launch.
+struct SolveCtl {
+  double tol2, delta;
+  int maxiter, budget;
+  int launch_iters;  // iterations of the current graph launch
+  int nan;           // a non-finite residual norm was seen
+  int nrhs, pad;
 };
 
 struct BlockPlan;

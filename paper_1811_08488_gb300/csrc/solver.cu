@@ -467,10 +467,17 @@ void block_precondition(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, int
 // ---------------------------------------------------------------------------
 // Outer solve
 // ---------------------------------------------------------------------------
+void SolverPlan::drop_graphs() {
+  if (loop) cudaGraphExecDestroy(loop);
+  loop = nullptr;
+  loop_key.clear();
+}
+
 SolverPlan::~SolverPlan() {
-  if (graph) cudaGraphExecDestroy(graph);
+  drop_graphs();
   if (host_scal) cudaFreeHost(host_scal);
   if (host_skip) cudaFreeHost(host_skip);
+  if (host_ctl) cudaFreeHost(host_ctl);
 }
 
 static SolverPlan *get_solver_plan(dwf_ctx *ctx, dwf_prec lo, int nrhs) {
@@ -506,6 +513,8 @@ static SolverPlan *get_solver_plan(dwf_ctx *ctx, dwf_prec lo, int nrhs) {
   DWF_CUDA_TRY(cudaMemset(sp->ocount.p, 0, sp->ocount.bytes));
   sp->skip_iter.ensure(sizeof(int) * nrhs);
   sp->skip_ru.ensure(sizeof(int) * nrhs);
+  sp->ctl.ensure(sizeof(SolveCtl));
+  DWF_CUDA_TRY(cudaMallocHost(&sp->host_ctl, sizeof(SolveCtl)));
   DWF_CUDA_TRY(cudaMallocHost(&sp->host_scal, sizeof(OuterScalars) * nrhs));
   DWF_CUDA_TRY(cudaMallocHost(&sp->host_skip, sizeof(int) * 2 * nrhs));
   slot = std::move(sp);
@@ -567,6 +576,92 @@ static void enqueue_reliable_update(SolveSetup &S, cudaStream_t st) {
                        (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo);
     outer_set_rz(A, S.nrhs, st);
   }
+}
+
+// The last node of a graph captured from one stream.
+static cudaGraphNode_t sink_of(cudaGraph_t g) {
+  size_t n = 0;
+  DWF_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  DWF_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &n));
+  std::vector<cudaGraphNode_t> sinks;
+  for (cudaGraphNode_t nd : nodes) {
+    size_t m = 0;
+    DWF_CUDA_TRY(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &m));
+    if (m == 0) sinks.push_back(nd);
+  }
+  DWF_REQUIRE(sinks.size() == 1, DWF_ERR_CUDA, "a captured graph body has no single last node");
+  return sinks[0];
+}
+
+// Capture the work that fn() enqueues on st into the empty graph g.
+template <class F>
+static void capture_into(cudaGraph_t g, cudaStream_t st, F fn) {
+  DWF_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+  try {
+    fn();
+  } catch (...) {
+    cudaGraph_t tmp;
+    cudaStreamEndCapture(st, &tmp);
+    throw;
+  }
+  cudaGraph_t out;
+  DWF_CUDA_TRY(cudaStreamEndCapture(st, &out));
+}
+
+// The device-driven outer loop as one executable graph:
+//   reset the launch's iteration count;
+//   while (h_loop) {
+//     one outer iteration of Algorithm 1 (all right-hand sides);
+//     control: per right-hand side, reliable update needed? loop on? (h_ru, h_loop)
+//     if (h_ru) { reliable update of those right-hand sides; mark the converged }
+//   }
+static void build_loop_graph(SolveSetup &S, cudaStream_t st) {
+  SolverPlan *sp = S.sp;
+  SolveCtl *ctl = sp->ctl.as<SolveCtl>();
+  OuterScalars *scal = sp->scal.as<OuterScalars>();
+  int *skip_ru = sp->skip_ru.as<int>(), *skip_iter = sp->skip_iter.as<int>();
+  cudaGraph_t top;
+  DWF_CUDA_TRY(cudaGraphCreate(&top, 0));
+  try {
+    cudaGraphConditionalHandle h_loop;
+    DWF_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault));
+    capture_into(top, st, [&] { solve_launch(ctl, st); });
+    cudaGraphNode_t head = sink_of(top);
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    DWF_CUDA_TRY(cudaGraphAddNode(&wnode, top, &head, nullptr, 1, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaGraphConditionalHandle h_ru;
+    DWF_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_ru, body, 0, cudaGraphCondAssignDefault));
+    capture_into(body, st, [&] {
+      enqueue_iteration(S, st);
+      solve_control(scal, ctl, skip_ru, h_loop, h_ru, st);
+    });
+    cudaGraphNode_t last = sink_of(body);
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_ru;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    DWF_CUDA_TRY(cudaGraphAddNode(&inode, body, &last, nullptr, 1, &ip));
+    cudaGraph_t rbody = ip.conditional.phGraph_out[0];
+    capture_into(rbody, st, [&] {
+      enqueue_reliable_update(S, st);
+      solve_post_ru(scal, ctl, skip_ru, skip_iter, h_loop, st);
+    });
+    DWF_CUDA_TRY(cudaGraphInstantiate(&sp->loop, top, 0));
+  } catch (...) {
+    cudaGraphDestroy(top);
+    throw;
+  }
+  cudaGraphDestroy(top);
 }
 
 // Compulsory bytes and device nanoseconds summed over the hop-kernel timer
@@ -653,139 +748,169 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   }
   outer_copy_p(lo, A, nrhs, st);
 
-  // graph of one iteration
-  bool use_graph = prm->use_graph != 0 && st != nullptr;
-  if (use_graph) {
+  // The outer loop. With a capturing stream (use_graph) it runs on the device:
+  // one CUDA graph holds a while-loop over the outer iteration, whose control
+  // kernel decides the reliable updates and convergence of every right-hand
+  // side after each iteration (an if-node runs the reliable update); the host
+  // only waits for the graph launch to end and reads the scalars. Otherwise
+  // the host drives the loop with eager launches, checking every few
+  // iterations.
+  const bool device_loop = prm->use_graph != 0 && st != nullptr;
+  const double tol2 = prm->tol * prm->tol;
+  std::vector<double> final_res(nrhs, -1.0);
+  std::vector<int> done(nrhs, 0), nru(nrhs, 0);
+  int host_syncs = 0;
+  dwf_status status = DWF_OK;
+  if (device_loop) {
     std::ostringstream key;
     key << (void *)bp << "/" << (bp ? bp->r.p : nullptr) << "/" << prm->inner_iters << "/"
         << prm->snake << "/" << plain << "/" << A.flexible << "/" << ctx->prof_on;
     for (int r = 0; r < nrhs; ++r) key << "/" << mf[r];
-    if (!sp->graph || sp->graph_key != key.str()) {
-      if (sp->graph) cudaGraphExecDestroy(sp->graph);
-      sp->graph = nullptr;
-      cudaGraph_t g;
-      DWF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      try {
-        enqueue_iteration(S, st);
-      } catch (...) {
-        cudaStreamEndCapture(st, &g);
-        throw;
+    if (!sp->loop || sp->loop_key != key.str()) {
+      sp->drop_graphs();
+      build_loop_graph(S, st);
+      sp->loop_key = key.str();
+    }
+    SolveCtl init{};
+    init.tol2 = tol2;
+    init.delta = prm->delta;
+    init.maxiter = prm->maxiter;
+    init.budget = kHistory;
+    init.nrhs = nrhs;
+    solve_start(sp->scal.as<OuterScalars>(), sp->ctl.as<SolveCtl>(), sp->skip_iter.as<int>(),
+                init, st);
+    while (true) {
+      DWF_CUDA_TRY(cudaGraphLaunch(sp->loop, st));
+      DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_scal, sp->scal.p, sizeof(OuterScalars) * nrhs,
+                                   cudaMemcpyDeviceToHost, st));
+      DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_ctl, sp->ctl.p, sizeof(SolveCtl),
+                                   cudaMemcpyDeviceToHost, st));
+      DWF_CUDA_TRY(cudaStreamSynchronize(st));
+      ++host_syncs;
+      if (sp->host_ctl->nan) {
+        status = DWF_ERR_NAN;
+        break;
       }
-      DWF_CUDA_TRY(cudaStreamEndCapture(st, &g));
-      DWF_CUDA_TRY(cudaGraphInstantiate(&sp->graph, g, 0));
-      cudaGraphDestroy(g);
-      sp->graph_key = key.str();
+      int open = 0, itmax = 0;
+      for (int r = 0; r < nrhs; ++r)
+        if (!sp->host_scal[r].done) {
+          ++open;
+          itmax = std::max(itmax, sp->host_scal[r].iter);
+        }
+      if (!open || itmax >= prm->maxiter) break;
     }
-  }
-
-  DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_scal, sp->scal.p, sizeof(OuterScalars) * nrhs,
-                               cudaMemcpyDeviceToHost, st));
-  DWF_CUDA_TRY(cudaStreamSynchronize(st));
-  std::vector<double> bb(nrhs), maxr(nrhs), final_res(nrhs, -1.0);
-  std::vector<int> done(nrhs, 0), seen(nrhs, 0), nru(nrhs, 0);
-  for (int r = 0; r < nrhs; ++r) {
-    bb[r] = sp->host_scal[r].bb;
-    maxr[r] = std::sqrt(sp->host_scal[r].rr);
-    if (bb[r] == 0.0) {  // zero source: x = 0 is exact
-      done[r] = 1;
-      final_res[r] = 0.0;
-      hs_iter[r] = 1;
+    for (int r = 0; r < nrhs; ++r) {
+      const OuterScalars &q = sp->host_scal[r];
+      done[r] = q.done;
+      nru[r] = q.nru;
+      if (q.done) final_res[r] = q.final_res;
+      hs_iter[r] = q.done;
     }
-  }
-  const double tol2 = prm->tol * prm->tol;
-  const bool debug = std::getenv("DWF_DEBUG") != nullptr;
-  int chunk = std::max(1, std::min(prm->check_every, 8));
-  dwf_status status = DWF_OK;
-  int total_iters = 0;
-  while (true) {
-    int active = 0;
-    for (int r = 0; r < nrhs; ++r) active += !done[r];
-    if (!active) break;
-    if (total_iters >= prm->maxiter) {
-      status = DWF_ERR_NOT_CONVERGED;
-      break;
-    }
-    DWF_CUDA_TRY(cudaMemcpyAsync(sp->skip_iter.p, hs_iter, sizeof(int) * nrhs,
-                                 cudaMemcpyHostToDevice, st));
-    const int n = std::min(chunk, prm->maxiter - total_iters);
-    for (int i = 0; i < n; ++i) {
-      if (use_graph)
-        DWF_CUDA_TRY(cudaGraphLaunch(sp->graph, st));
-      else
-        enqueue_iteration(S, st);
-    }
-    total_iters += n;
+  } else {
     DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_scal, sp->scal.p, sizeof(OuterScalars) * nrhs,
                                  cudaMemcpyDeviceToHost, st));
     DWF_CUDA_TRY(cudaStreamSynchronize(st));
-    if (debug) {
-      for (int r = 0; r < nrhs; ++r) {
-        const OuterScalars &q = sp->host_scal[r];
-        std::fprintf(stderr, "[dwf] rhs %d iter %d rr %.6e rz %.6e rz_new %.6e pAp %.6e alpha %.6e "
-                     "beta %.6e bb %.6e\n", r, q.iter, q.rr, q.rz, q.rz_new, q.pAp, q.alpha,
-                     q.beta, q.bb);
-      }
-    }
-    bool any_ru = false;
-    std::vector<int> conv_cand(nrhs, 0);
-    int min_pred = 1 << 30;
+    std::vector<double> bb(nrhs), maxr(nrhs);
+    std::vector<int> seen(nrhs, 0);
     for (int r = 0; r < nrhs; ++r) {
-      hs_ru[r] = 1;
-      if (done[r]) continue;
-      const OuterScalars &sc = sp->host_scal[r];
-      bool need = false;
-      double rr_last = sc.rr, rr_first = -1;
-      for (int it = seen[r]; it < sc.iter; ++it) {
-        const double rr = sc.hist_rr[it % kHistory];
-        if (rr_first < 0) rr_first = rr;
-        if (!std::isfinite(rr)) {
-          status = DWF_ERR_NAN;
-        }
-        if (rr <= tol2 * bb[r]) conv_cand[r] = 1;
-        if (std::sqrt(rr) < prm->delta * maxr[r]) need = true;
-        maxr[r] = std::max(maxr[r], std::sqrt(rr));
-        rr_last = rr;
-      }
-      const int adv = sc.iter - seen[r];
-      seen[r] = sc.iter;
-      if (conv_cand[r]) need = true;
-      if (need) {
-        hs_ru[r] = 0;
-        any_ru = true;
-      }
-      // predict the iterations left from the last chunk's rate of decrease
-      if (adv > 0 && rr_first > 0 && rr_last > 0 && rr_last < rr_first) {
-        const double rate = std::log(rr_last / rr_first) / adv;
-        const double left = std::log(tol2 * bb[r] / rr_last) / rate;
-        if (left > 0 && left < 1e9) min_pred = std::min(min_pred, (int)std::ceil(left));
+      bb[r] = sp->host_scal[r].bb;
+      maxr[r] = std::sqrt(sp->host_scal[r].rr);
+      if (bb[r] == 0.0) {  // zero source: x = 0 is exact
+        done[r] = 1;
+        final_res[r] = 0.0;
+        hs_iter[r] = 1;
       }
     }
-    if (status == DWF_ERR_NAN) break;
-    // never more iterations between checks than the |r|^2 ring holds
-    chunk = std::max(1, std::min(std::min(prm->check_every, kHistory), min_pred));
-    if (any_ru) {
-      DWF_CUDA_TRY(cudaMemcpyAsync(sp->skip_ru.p, hs_ru, sizeof(int) * nrhs,
+    const bool debug = std::getenv("DWF_DEBUG") != nullptr;
+    int chunk = std::max(1, std::min(prm->check_every, 8));
+    int total_iters = 0;
+    while (true) {
+      int active = 0;
+      for (int r = 0; r < nrhs; ++r) active += !done[r];
+      if (!active) break;
+      if (total_iters >= prm->maxiter) {
+        status = DWF_ERR_NOT_CONVERGED;
+        break;
+      }
+      DWF_CUDA_TRY(cudaMemcpyAsync(sp->skip_iter.p, hs_iter, sizeof(int) * nrhs,
                                    cudaMemcpyHostToDevice, st));
-      enqueue_reliable_update(S, st);
+      const int n = std::min(chunk, prm->maxiter - total_iters);
+      for (int i = 0; i < n; ++i) enqueue_iteration(S, st);
+      total_iters += n;
       DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_scal, sp->scal.p, sizeof(OuterScalars) * nrhs,
                                    cudaMemcpyDeviceToHost, st));
       DWF_CUDA_TRY(cudaStreamSynchronize(st));
+      ++host_syncs;
+      if (debug) {
+        for (int r = 0; r < nrhs; ++r) {
+          const OuterScalars &q = sp->host_scal[r];
+          std::fprintf(stderr, "[dwf] rhs %d iter %d rr %.6e rz %.6e rz_new %.6e pAp %.6e alpha %.6e "
+                       "beta %.6e bb %.6e\n", r, q.iter, q.rr, q.rz, q.rz_new, q.pAp, q.alpha,
+                       q.beta, q.bb);
+        }
+      }
+      bool any_ru = false;
+      std::vector<int> conv_cand(nrhs, 0);
+      int min_pred = 1 << 30;
       for (int r = 0; r < nrhs; ++r) {
-        if (hs_ru[r]) continue;
-        if (debug)
-          std::fprintf(stderr, "[dwf] rhs %d reliable update: true rr %.6e rz %.6e\n", r,
-                       sp->host_scal[r].rr, sp->host_scal[r].rz);
-        nru[r] += 1;
-        const double rr = sp->host_scal[r].rr;
-        maxr[r] = std::sqrt(rr);
-        if (!std::isfinite(rr)) status = DWF_ERR_NAN;
-        if (rr <= tol2 * bb[r]) {
-          done[r] = 1;
-          hs_iter[r] = 1;
-          final_res[r] = std::sqrt(rr / bb[r]);
+        hs_ru[r] = 1;
+        if (done[r]) continue;
+        const OuterScalars &sc = sp->host_scal[r];
+        bool need = false;
+        double rr_last = sc.rr, rr_first = -1;
+        for (int it = seen[r]; it < sc.iter; ++it) {
+          const double rr = sc.hist_rr[it % kHistory];
+          if (rr_first < 0) rr_first = rr;
+          if (!std::isfinite(rr)) {
+            status = DWF_ERR_NAN;
+          }
+          if (rr <= tol2 * bb[r]) conv_cand[r] = 1;
+          if (std::sqrt(rr) < prm->delta * maxr[r]) need = true;
+          maxr[r] = std::max(maxr[r], std::sqrt(rr));
+          rr_last = rr;
+        }
+        const int adv = sc.iter - seen[r];
+        seen[r] = sc.iter;
+        if (conv_cand[r]) need = true;
+        if (need) {
+          hs_ru[r] = 0;
+          any_ru = true;
+        }
+        // predict the iterations left from the last chunk's rate of decrease
+        if (adv > 0 && rr_first > 0 && rr_last > 0 && rr_last < rr_first) {
+          const double rate = std::log(rr_last / rr_first) / adv;
+          const double left = std::log(tol2 * bb[r] / rr_last) / rate;
+          if (left > 0 && left < 1e9) min_pred = std::min(min_pred, (int)std::ceil(left));
         }
       }
       if (status == DWF_ERR_NAN) break;
+      // never more iterations between checks than the |r|^2 ring holds
+      chunk = std::max(1, std::min(std::min(prm->check_every, kHistory), min_pred));
+      if (any_ru) {
+        DWF_CUDA_TRY(cudaMemcpyAsync(sp->skip_ru.p, hs_ru, sizeof(int) * nrhs,
+                                     cudaMemcpyHostToDevice, st));
+        enqueue_reliable_update(S, st);
+        DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_scal, sp->scal.p, sizeof(OuterScalars) * nrhs,
+                                     cudaMemcpyDeviceToHost, st));
+        DWF_CUDA_TRY(cudaStreamSynchronize(st));
+        ++host_syncs;
+        for (int r = 0; r < nrhs; ++r) {
+          if (hs_ru[r]) continue;
+          if (debug)
+            std::fprintf(stderr, "[dwf] rhs %d reliable update: true rr %.6e rz %.6e\n", r,
+                         sp->host_scal[r].rr, sp->host_scal[r].rz);
+          nru[r] += 1;
+          const double rr = sp->host_scal[r].rr;
+          maxr[r] = std::sqrt(rr);
+          if (!std::isfinite(rr)) status = DWF_ERR_NAN;
+          if (rr <= tol2 * bb[r]) {
+            done[r] = 1;
+            hs_iter[r] = 1;
+            final_res[r] = std::sqrt(rr / bb[r]);
+          }
+        }
+        if (status == DWF_ERR_NAN) break;
+      }
     }
   }
   // unconverged right-hand sides: fold x_lo in and measure the true residual
@@ -801,10 +926,11 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
     DWF_CUDA_TRY(cudaMemcpyAsync(sp->host_scal, sp->scal.p, sizeof(OuterScalars) * nrhs,
                                  cudaMemcpyDeviceToHost, st));
     DWF_CUDA_TRY(cudaStreamSynchronize(st));
+    ++host_syncs;
     for (int r = 0; r < nrhs; ++r)
       if (!done[r]) {
         nru[r] += 1;
-        final_res[r] = std::sqrt(sp->host_scal[r].rr / bb[r]);
+        final_res[r] = std::sqrt(sp->host_scal[r].rr / sp->host_scal[r].bb);
       }
   }
   // output
@@ -833,6 +959,8 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
       info[r].true_resid = final_res[r];
       info[r].seconds = secs;
       info[r].dslash_gbs = dslash_gbs;
+      info[r].host_syncs = host_syncs;
+      info[r].device_loop = device_loop ? 1 : 0;
     }
     all_conv &= final_res[r] >= 0 && final_res[r] <= prm->tol;
   }

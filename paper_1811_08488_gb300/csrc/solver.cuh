@@ -77,10 +77,13 @@ struct SolverPlan {
   DevBuf xlo, rlo, p, Ap, z;
   DevBuf wlo, w64;  // operator temporaries
   DevBuf scal, partials, counters, opart, ocount, skip_iter, skip_ru;
+  DevBuf ctl;  // SolveCtl of the device-driven loop
   OuterScalars *host_scal = nullptr;
   int *host_skip = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  std::string graph_key;
+  SolveCtl *host_ctl = nullptr;
+  cudaGraphExec_t loop = nullptr;  // the device-driven outer loop (one graph)
+  std::string loop_key;
+  void drop_graphs();
   ~SolverPlan();
 };
 

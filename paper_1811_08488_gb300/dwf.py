@@ -56,7 +56,7 @@ class SolveInfo(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int),
                 ("reliable_updates", C.c_int), ("converged", C.c_int),
                 ("true_resid", C.c_double), ("seconds", C.c_double),
-                ("dslash_gbs", C.c_double)]
+                ("dslash_gbs", C.c_double), ("host_syncs", C.c_int), ("device_loop", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -17,6 +17,10 @@ Layouts (all complex128, C order):
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import multiprocessing as mp
+import os
+
 import numpy as np
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -35,16 +39,21 @@ def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
     return z
 
 
-def uniform(seed: int, count: int) -> np.ndarray:
-    """Uniform deviates in the open interval (0, 1) from the top 53 bits."""
-    z = splitmix64(seed, count)
+def uniform(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Uniform deviates in the open interval (0, 1) from the top 53 bits
+    (draws offset .. offset+count-1 of the stream)."""
+    z = splitmix64(seed, count, offset)
     return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
 
 
-def normal(seed: int, count: int) -> np.ndarray:
-    """Standard normal deviates by Box-Muller on pairs (u1, u2)."""
+def normal(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Standard normal deviates by Box-Muller on pairs (u1, u2): deviates
+    offset .. offset+count-1 of stream `seed` (offset even, so that a slice
+    starts on a pair)."""
+    if offset % 2:
+        raise ValueError("normal(): offset must be even")
     n2 = (count + 1) // 2
-    u = uniform(seed, 2 * n2).reshape(n2, 2)
+    u = uniform(seed, 2 * n2, offset).reshape(n2, 2)
     rad = np.sqrt(-2.0 * np.log(u[:, 0]))
     ang = 2.0 * np.pi * u[:, 1]
     out = np.empty((n2, 2))
@@ -88,7 +97,29 @@ def su3_exp(h: np.ndarray, eps: float) -> np.ndarray:
     return U
 
 
-def gauge_field(dims, eps: float, seed: int) -> np.ndarray:
+# Large fields are drawn in slabs by a pool of worker processes (started with
+# "spawn", so a process that already uses a GPU can call this safely). Every
+# slab reads its own part of the counter-based stream, so the result is the
+# same array as the serial draw.
+PARALLEL_MIN = 1 << 24  # deviates; smaller draws stay in this process
+
+
+def _pool_workers() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def _gauge_slab(dims, eps, seed, t):
+    Lx, Ly, Lz, Lt = dims
+    per = Lx * Ly * Lz * 4 * 8
+    h = normal(seed, per, t * per).reshape(1, Lz, Ly, Lx, 4, 8)
+    return su3_exp(h, eps)
+
+
+def _normal_slab(seed, count, offset):
+    return normal(seed, count, offset)
+
+
+def gauge_field(dims, eps: float, seed: int, parallel_min: int = PARALLEL_MIN) -> np.ndarray:
     """Synthetic SU(3) links U = exp(i eps H), H Gaussian traceless Hermitian.
 
     dims = (Lx, Ly, Lz, Lt). Returns U[t][z][y][x][mu][3][3] complex128.
@@ -96,8 +127,12 @@ def gauge_field(dims, eps: float, seed: int) -> np.ndarray:
     """
     Lx, Ly, Lz, Lt = dims
     n = Lx * Ly * Lz * Lt * 4 * 8
-    h = normal(seed, n).reshape(Lt, Lz, Ly, Lx, 4, 8)
-    return su3_exp(h, eps)
+    if n < parallel_min or _pool_workers() == 1 or Lt == 1:
+        h = normal(seed, n).reshape(Lt, Lz, Ly, Lx, 4, 8)
+        return su3_exp(h, eps)
+    with cf.ProcessPoolExecutor(_pool_workers(), mp_context=mp.get_context("spawn")) as ex:
+        slabs = list(ex.map(_gauge_slab, [dims] * Lt, [eps] * Lt, [seed] * Lt, range(Lt)))
+    return np.concatenate(slabs, axis=0)
 
 
 def unit_gauge(dims) -> np.ndarray:
@@ -114,7 +149,7 @@ def random_su3(shape, seed: int) -> np.ndarray:
     return su3_exp(h, 2.0)
 
 
-def half_field(dims, Ls: int, seed: int) -> np.ndarray:
+def half_field(dims, Ls: int, seed: int, parallel_min: int = PARALLEL_MIN) -> np.ndarray:
     """Gaussian complex parity half field psi[s][t][z][y][xh][4][3].
 
     Real and imaginary parts are independent N(0,1); they are drawn as
@@ -123,8 +158,17 @@ def half_field(dims, Ls: int, seed: int) -> np.ndarray:
     Lx, Ly, Lz, Lt = dims
     shape = (Ls, Lt, Lz, Ly, Lx // 2, 4, 3)
     n = int(np.prod(shape))
-    z = normal(seed, 2 * n).reshape(n, 2)
-    return (z[:, 0] + 1j * z[:, 1]).reshape(shape)
+    if 2 * n < parallel_min or _pool_workers() == 1:
+        z = normal(seed, 2 * n).reshape(n, 2)
+        return (z[:, 0] + 1j * z[:, 1]).reshape(shape)
+    per = 2 * n // Ls  # deviates of one s slice
+    with cf.ProcessPoolExecutor(_pool_workers(), mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_normal_slab, [seed] * Ls, [per] * Ls, [s * per for s in range(Ls)]))
+    out = np.empty(shape, dtype=np.complex128)
+    for s, z in enumerate(parts):
+        z = z.reshape(-1, 2)
+        out[s] = (z[:, 0] + 1j * z[:, 1]).reshape(shape[1:])
+    return out
 
 
 def log_spaced_masses(lo: float, hi: float, n: int) -> np.ndarray:

@@ -7,6 +7,10 @@ that hold at any size.
 * Moebius 16^3 x 32 x 12 with 16 right-hand sides of log-spaced masses in one
   call (per-rhs early exit): every rhs converges, lighter masses need more
   iterations, oracle residual of the lightest.
+* Moebius 24^3 x 64 x 16 (m_f 0.003, the benchmark's headline solve, MSPCG
+  with 12^3 x 16 blocks, k = 6, FP16 inner): the oracle recomputes the FP64
+  residual of the GPU solution over the whole lattice, slab by slab on the
+  host's cores.
 * The multisplitting preconditioner at full size is block diagonal: z on a
   block depends only on r on that block.
 """
@@ -68,6 +72,25 @@ def test_mobius_16x16x16x32_mspcg_benchmark_solve():
                         tol=1e-10)
     assert st == 0 and info[0]["converged"]
     assert oracle_resid(act, op.gauge_to_mu_major(U), x[0], srcs[0], mf) <= 1e-10
+
+
+def test_mobius_24x24x24x64_mspcg_oracle_residual():
+    """The benchmark's headline solve. Host memory: the inputs and the solution
+    (about 4 GB) and the oracle's worker processes (about 1.5 GB each, up to 16
+    of them). The oracle's FP64 |b - A x| / |b| must be <= 1e-10 and agree with
+    the library's own FP64 recomputation."""
+    from oracle import slabs
+    w, act, U, srcs, ctx = load("mobius_24^3x64x16")
+    mf = w["mf"][0]
+    st, info, x = solve(ctx, srcs, [mf], inner_iters=6, block=w["block"], inner="fp16",
+                        tol=1e-10)
+    ctx.close()
+    assert st == 0 and info[0]["converged"] and info[0]["true_resid"] <= 1e-10
+    b = srcs[0]
+    r = b - slabs.mdagm_half(act, U, x[0], mf, slab=4)
+    res = float(np.sqrt(np.vdot(r, r).real / np.vdot(b, b).real))
+    assert res <= 1e-10
+    assert abs(res - info[0]["true_resid"]) <= 1e-3 * res
 
 
 def test_mobius_16_rhs_log_spaced_masses_one_call():

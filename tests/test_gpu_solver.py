@@ -91,6 +91,40 @@ def test_multi_rhs_uneven_masses():
         assert oracle_resid(act, U, x[r], srcs[r], masses[r]) <= 1e-10
 
 
+@pytest.mark.parametrize("kw", [dict(inner_iters=0),
+                                dict(inner_iters=4, block=(4, 4, 4, 4), inner="fp16")])
+def test_device_decided_early_exit_uneven_iteration_counts(kw):
+    """Four right-hand sides in one call whose outer-iteration counts differ by
+    more than 2x (m_f 0.005 to 1.0, and a zero source that x = 0 solves): the
+    device decides every right-hand side's reliable updates and convergence
+    after each iteration and skips the finished ones, the host waits once per
+    graph launch, and every right-hand side meets the oracle's FP64 residual
+    bound. The host-driven loop (use_graph = 0) reaches the same bound with
+    more host waits."""
+    act, Uc, U, ctx = setup((8, 8, 8, 8), 8, 1.5, 0.5, 0.4, 1006)
+    masses = [0.005, 0.1, 1.0, 0.02]
+    srcs = [syn.half_field(act.dims, act.Ls, 2006 + r) for r in range(3)]
+    srcs.append(np.zeros_like(srcs[0]))
+    st, info, x = run(ctx, srcs, masses, tol=1e-10, **kw)
+    assert st == 0
+    its = [i["outer_iters"] for i in info]
+    assert its[3] == 0 and info[3]["converged"] and info[3]["true_resid"] == 0.0
+    assert max(its[:3]) >= 2 * min(its[:3]), its
+    for r in range(3):
+        assert info[r]["converged"], info[r]
+        assert oracle_resid(act, U, x[r], srcs[r], masses[r]) <= 1e-10
+    assert all(i["device_loop"] == 1 for i in info)
+    syncs = info[0]["host_syncs"]
+    assert 1 <= syncs <= max(its) // 256 + 2, (syncs, its)
+    st2, info2, x2 = run(ctx, srcs, masses, tol=1e-10, use_graph=0, **kw)
+    assert st2 == 0 and all(i["device_loop"] == 0 for i in info2)
+    for r in range(3):
+        assert oracle_resid(act, U, x2[r], srcs[r], masses[r]) <= 1e-10
+    assert info2[0]["host_syncs"] > syncs
+    print(f"outer iterations {its}, host waits: device-driven {syncs}, "
+          f"host-driven {info2[0]['host_syncs']}")
+
+
 def test_snake_terms_matter_on_gpu():
     act, Uc, U, ctx = setup((8, 8, 8, 8), 8, 1.5, 0.5, 0.45, 1004)
     src = syn.half_field(act.dims, act.Ls, 2004)

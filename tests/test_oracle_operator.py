@@ -40,6 +40,17 @@ def test_splitmix64_published_values():
     assert got == want
 
 
+def test_parallel_draws_equal_serial_draws():
+    """Large fields are drawn in slabs by worker processes; each slab reads its
+    own part of the counter-based stream, so the arrays are the same."""
+    dims = (4, 4, 2, 6)
+    assert np.array_equal(syn.gauge_field(dims, 0.4, 3),
+                          syn.gauge_field(dims, 0.4, 3, parallel_min=1))
+    assert np.array_equal(syn.half_field(dims, 5, 3), syn.half_field(dims, 5, 3, parallel_min=1))
+    n = syn.normal(9, 20)
+    assert np.array_equal(syn.normal(9, 8, 12), n[12:])
+
+
 def test_gauge_is_su3():
     U = syn.gauge_field((4, 4, 4, 4), 0.4, 5)
     I = np.eye(3)
@@ -400,6 +411,42 @@ def test_schur_solution_solves_full_system(brute):
     psi_o = op.odd_reconstruct(act, U, psi_e, phi_o, mf)
     psi = psi_e + psi_o
     assert np.abs(D @ psi.reshape(-1) - phi.reshape(-1)).max() < 1e-11
+
+
+def test_symmetric_schur_form_dense(brute):
+    """D_sym = 1 - M_5^-1 M^4_eo M_5^-1 M^4_oe equals D_ee^-1 (D_ee - D_eo D_oo^-1
+    D_oe) built from the dense full matrix, its adjoint is the conjugate
+    transpose, and A_sym = D_sym^dag D_sym is Hermitian positive definite."""
+    act, U, mf, D, e, o = brute
+    Dee, Deo, Doe, Doo = D[np.ix_(e, e)], D[np.ix_(e, o)], D[np.ix_(o, e)], D[np.ix_(o, o)]
+    Dsym_dense = np.linalg.solve(Dee, Dee - Deo @ np.linalg.solve(Doo, Doe))
+    even = op.parity_mask(act.shape4) == 0
+    mask5 = np.broadcast_to(even[None, :, :, :, :, None, None], act.shape5)
+    Dsym, idx = dense(lambda v: op.mpc_sym(act, U, v, mf), act.shape5, mask5)
+    assert np.abs(Dsym - Dsym_dense).max() < 1e-12
+    Dsymd, _ = dense(lambda v: op.mpc_sym(act, U, v, mf, True), act.shape5, mask5)
+    assert np.abs(Dsymd - Dsym_dense.conj().T).max() < 1e-12
+    A, _ = dense(lambda v: op.mdagm_sym(act, U, v, mf), act.shape5, mask5)
+    assert np.abs(A - Dsym_dense.conj().T @ Dsym_dense).max() < 1e-12
+    assert np.linalg.eigvalsh(0.5 * (A + A.conj().T)).min() > 0
+
+
+@pytest.mark.parametrize("schur", ["asym", "sym"])
+def test_normal_equation_solution_solves_full_system(brute, schur):
+    """The normal equation of either Schur form, with its right-hand side
+    normal_source, gives the even half of the solution of D psi = phi."""
+    act, U, mf, D, e, o = brute
+    phi = rand5(act)
+    phi_e, phi_o = op.restrict_parity(phi, 0), op.restrict_parity(phi, 1)
+    b = op.normal_source(act, U, phi_e, phi_o, mf, schur)
+    even = op.parity_mask(act.shape4) == 0
+    mask5 = np.broadcast_to(even[None, :, :, :, :, None, None], act.shape5)
+    A, idx = dense(lambda v: op.normal_op(schur)(act, U, v, mf), act.shape5, mask5)
+    psi_e = np.zeros(phi.size, dtype=complex)
+    psi_e[idx] = np.linalg.solve(A, b.reshape(-1)[idx])
+    psi_e = psi_e.reshape(act.shape5)
+    psi = psi_e + op.odd_reconstruct(act, U, psi_e, phi_o, mf)
+    assert np.abs(D @ psi.reshape(-1) - phi.reshape(-1)).max() < 1e-10
 
 
 def test_pointwise_matches_full_array():

@@ -134,6 +134,26 @@ def test_inner_cg_is_krylov_optimal(small_block, k):
     assert np.abs(z - want).max() < 1e-9 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("eps", [0.5, 0.1, 0.02])
+def test_inner_cg_with_residual_stop(small_block, eps):
+    """cg_stop takes the first k whose CG residual is <= eps |r|: its result is
+    the Krylov-optimal solution in K_k (dense Galerkin), whose residual
+    |r - A_s z| meets the stop, while the optimal one in K_{k-1} does not."""
+    act, Aop, As, idx, r = small_block
+    rv = r.reshape(-1)[idx]
+    z, k = sv.cg_stop(Aop, r, 50, eps)
+    assert 1 <= k < 50
+    want = krylov_optimal(As, rv, k)
+    assert np.abs(z.reshape(-1)[idx] - want).max() < 1e-9 * np.abs(want).max()
+    assert np.linalg.norm(rv - As @ want) <= eps * np.linalg.norm(rv) * (1 + 1e-9)
+    if k > 1:
+        prev = krylov_optimal(As, rv, k - 1)
+        assert np.linalg.norm(rv - As @ prev) > eps * np.linalg.norm(rv)
+    # eps = 0 is the fixed-count solve
+    z0, k0 = sv.cg_stop(Aop, r, 3, 0.0)
+    assert k0 == 3 and np.abs(z0 - sv.cg_fixed(Aop, r, 3)).max() == 0.0
+
+
 def test_inner_cg_many_iterations_is_exact(small_block):
     act, Aop, As, idx, r = small_block
     z = sv.cg_fixed(Aop, r, 120).reshape(-1)[idx]
@@ -182,6 +202,28 @@ def test_block_partition_covers_even_sites_once(four_blocks):
     assert np.array_equal(np.sort(allsel), np.arange(len(idx)))
 
 
+def test_ms_precondition_symmetric_form_is_block_diagonal_stack(four_blocks):
+    """The same stacking for the symmetric Schur form: on every block the
+    Krylov-optimal solution with the dense sub-matrix of A_sym, with and
+    without an inner residual stop (the stop applied per block)."""
+    act, U, mf, A, idx, block, sels, r = four_blocks
+    Asym, idx2 = dense_on(lambda v: op.mdagm_sym(act, U, v, mf), act, np.ones(act.shape4, bool))
+    assert np.array_equal(idx, idx2)
+    rv = r.reshape(-1)[idx]
+    for inner_tol in (0.0, 0.3):
+        z = sv.ms_precondition(act, U, r, mf, block, 4, form="definition", schur="sym",
+                               inner_tol=inner_tol).reshape(-1)[idx]
+        for origin, _, sel in sels:
+            As = Asym[np.ix_(sel, sel)]
+            k = 4
+            if inner_tol:
+                k = next(j for j in range(1, 5)
+                         if np.linalg.norm(rv[sel] - As @ krylov_optimal(As, rv[sel], j))
+                         <= inner_tol * np.linalg.norm(rv[sel]) or j == 4)
+            want = krylov_optimal(As, rv[sel], k)
+            assert np.abs(z[sel] - want).max() < 1e-11 * np.abs(want).max(), (origin, inner_tol)
+
+
 @pytest.mark.parametrize("form", ["definition", "box"])
 @pytest.mark.parametrize("k", [1, 2, 3, 5])
 def test_ms_precondition_is_block_diagonal_stack(four_blocks, form, k):
@@ -210,6 +252,23 @@ def test_ms_precondition_truncated_is_block_diagonal_stack(four_blocks):
 
 
 # ----------------------------------------------------------------------------
+# A on large lattices, slab by slab (oracle/slabs.py)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("antiperiodic", [True, False])
+def test_slab_evaluation_equals_whole_lattice(antiperiodic):
+    """A x evaluated in t slabs of 2 rows, each on a small periodic lattice
+    with a four-row halo and the antiperiodic sign folded into the links,
+    equals op.mdagm on the whole lattice (A has range 4)."""
+    from oracle import slabs
+    act = op.Action(dims=(4, 2, 2, 12), Ls=3, antiperiodic=antiperiodic, **MOB)
+    Uc = syn.gauge_field(act.dims, 0.5, 31)
+    x = op.full_to_half(rand_even(act), 0)
+    want = op.full_to_half(op.mdagm(act, op.gauge_to_mu_major(Uc), op.half_to_full(x, 0), 0.04), 0)
+    got = slabs.mdagm_half(act, Uc, x, 0.04, slab=2, workers=2)
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+# ----------------------------------------------------------------------------
 # MSPCG (Algorithm 1 with the multisplitting preconditioner)
 # ----------------------------------------------------------------------------
 def test_mspcg_solves_and_matches_dense():
@@ -225,6 +284,26 @@ def test_mspcg_solves_and_matches_dense():
     assert np.abs(x.reshape(-1)[idx] - xd).max() <= 10 * cond * 1e-10 * np.abs(xd).max()
     xc, itc, _ = sv.cg(lambda v: op.mdagm(act, U, v, mf), b, 1e-10)
     assert it < itc
+
+
+def test_mspcg_symmetric_form_and_inner_stop_give_the_full_system_solution():
+    """MSPCG on the normal equation of the symmetric form, and with an inner
+    residual stop, reaches the same even solution of D psi = phi as the paper's
+    form (both normal equations have it as their unique solution)."""
+    act = op.Action(dims=(4, 2, 2, 4), Ls=4, **MOB)
+    U = gauge(act, eps=0.5, seed=8)
+    mf = 0.05
+    phi = RNG.normal(size=act.shape5) + 1j * RNG.normal(size=act.shape5)
+    phi_e, phi_o = op.restrict_parity(phi, 0), op.restrict_parity(phi, 1)
+    sols = []
+    for schur, inner_tol in (("asym", 0.0), ("sym", 0.0), ("asym", 0.2)):
+        b = op.normal_source(act, U, phi_e, phi_o, mf, schur)
+        x, it, res = sv.mspcg(act, U, b, mf, (2, 2, 2, 2), 4, 1e-11, schur=schur,
+                              inner_tol=inner_tol)
+        assert res <= 1e-11
+        sols.append(x)
+    for x in sols[1:]:
+        assert np.abs(x - sols[0]).max() < 1e-8 * np.abs(sols[0]).max()
 
 
 def test_mspcg_one_block_large_k_converges_at_once():
