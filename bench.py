@@ -145,12 +145,28 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 def cpu_model() -> str:
     try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
                 return line.split(":", 1)[1].strip()
     except OSError:
         pass
     return platform.processor() or platform.machine()
+
+
+ONE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def one_thread():
+    """Limit numpy's BLAS thread pools to one thread (threadpoolctl when it is
+    installed; the worker processes also start with the thread-count variables
+    set to 1). The oracle's elementwise numpy arithmetic is single-threaded."""
+    try:
+        import threadpoolctl
+        return threadpoolctl.threadpool_limits(1)
+    except ImportError:
+        import contextlib
+        return contextlib.nullcontext()
 
 
 def _oracle_inputs(name):
@@ -188,11 +204,10 @@ def oracle_one_core_jobs():
     * a full FP64 plain-CG solve of the Shamir 8^4 x 8 workload to 1e-10;
     * one A = D_PC^+ D_PC application on the 16^3 x 32 x 12 lattice;
     * one A_s application on a 6^3 x 8 block box of the headline workload."""
-    import threadpoolctl
     from oracle import dwf_operator as op
     from oracle import solvers as sv
     out = {}
-    with threadpoolctl.threadpool_limits(1):
+    with one_thread():
         w, act, Uc, src = _oracle_inputs("shamir_8^4x8")
         U = op.gauge_to_mu_major(Uc)
         b = op.half_to_full(src, 0)
@@ -273,8 +288,7 @@ def reference_sample(inputs):
     block box of the headline workload on one core (measured), scaled per 5D
     site to the headline MSPCG solve with the recorded GB300 outer-iteration
     count. `inputs` (oracle_block_inputs) are drawn once, outside the steps."""
-    import threadpoolctl
-    with threadpoolctl.threadpool_limits(1):
+    with one_thread():
         t, box = oracle_block_sample(WORKLOAD, (6, 6, 6, 8), inputs)
     from paper_1811_08488_gb300 import synthetic as syn
     block = syn.WORKLOADS[WORKLOAD]["block"]
@@ -858,8 +872,15 @@ def main():
     pool, fut = None, None
     want_cpu = world == 1 and not args.no_cpu_baseline
     if want_cpu:
+        saved = {k: os.environ.get(k) for k in ONE_THREAD_ENV}
+        os.environ.update({k: "1" for k in ONE_THREAD_ENV})
         pool = cf.ProcessPoolExecutor(1, mp_context=mp.get_context("spawn"))
         fut = pool.submit(oracle_one_core_jobs)
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
     dist = None
     if world > 1:

@@ -127,12 +127,22 @@ typedef struct {
   int flexible;       /* 1: flexible PCG, beta = <r_new - r, z_new> / <r, z>    
                        * (Polak-Ribiere); 0: Algorithm 1's <r_new, z_new> /   
                        * <r, z> (Fletcher-Reeves)                             */
+  int schur;          /* normal equation solved: 0 = D_PC^+ D_PC (the paper's   
+                       * Schur complement D_PC = M_5 - M^4_eo M_5^-1 M^4_oe),   
+                       * 1 = D_sym^+ D_sym with the symmetric form             
+                       * D_sym = 1 - M_5^-1 M^4_eo M_5^-1 M^4_oe = M_5^-1 D_PC; 
+                       * both outer operator and block operator follow it     */
+  double inner_tol;   /* 0: every block runs inner_iters CG iterations (the     
+                       * paper's fixed count); > 0: a block stops as soon as    
+                       * its inner residual fell to inner_tol times its start  
+                       * (at most inner_iters iterations)                     */
 } dwf_solver_params;
 
 /* Per right-hand-side result of mspcg_solve. */
 typedef struct {
   int outer_iters;       /* outer (Algorithm 1) iterations                   */
-  int inner_iters_total; /* outer_iters * k                                  */
+  int inner_iters_total; /* inner CG iterations over the solve, averaged over
+                          * the blocks (outer_iters * k without inner_tol)  */
   int reliable_updates;  /* FP64 residual recomputations                     */
   int converged;         /* 1 when true_resid <= tol                         */
   double true_resid;     /* |b - A x| / |b| recomputed in FP64               */
@@ -177,7 +187,8 @@ const char *dwf_last_error(const dwf_ctx *ctx);
 
 /* Fill *p with the defaults: tol 1e-10, maxiter 100000, inner_iters 6,
  * block = {0,0,0,0} (must be set for MSPCG), outer FP32, inner FP16,
- * delta 0.001, snake 1, use_graph 1, io_on_host 0, check_every 10, flexible 0. */
+ * delta 0.001, snake 1, use_graph 1, io_on_host 0, check_every 10, flexible 0,
+ * schur 0, inner_tol 0. */
 void dwf_solver_params_default(dwf_solver_params *p);
 
 /* Load the gauge field U (layout above; host pointer if on_device == 0): the
@@ -258,6 +269,29 @@ dwf_status dwf_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec,
 dwf_status dwf_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even,
                            const void *phi_odd, dwf_prec prec, int nrhs,
                            const double *mf, void *stream);
+
+/* The symmetric Schur form, a variant of the paper's D_PC (eq.
+ * (dirac_equation)) with the diagonal block divided out:
+ *   dagger = 0: out = D_sym in = in - M_5^-1 M^4_eo M_5^-1 M^4_oe in (= M_5^-1 D_PC in)
+ *   dagger = 1: out = D_sym^+ in = in - (M^4_oe)^+ M_5^-+ (M^4_eo)^+ M_5^-+ in
+ * on even native fields (DWF_FP64 or DWF_FP32). D_sym psi_e = M_5^-1 phi_hat_e
+ * has the same solution as D_PC psi_e = phi_hat_e. Uses the context's operator
+ * temporaries. Errors: INVALID_ARG, NO_GAUGE, CUDA. */
+dwf_status dwf_mpc_sym(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec,
+                       int nrhs, const double *mf, void *stream);
+
+/* out = D_sym^+ D_sym in, the normal operator mspcg_solve iterates on with
+ * params->schur = 1 (same arguments and errors as dwf_mdagm). */
+dwf_status dwf_mdagm_sym(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec, int nrhs,
+                         const double *mf, void *stream);
+
+/* Right-hand side of the symmetric form's normal equation for D psi = phi:
+ *   b_even = D_sym^+ M_5^-1 phi_hat_e,  phi_hat_e = phi_e - M^4_eo M_5^-1 phi_o
+ * (same arguments and errors as dwf_source_prep; solve with params->schur = 1,
+ * then dwf_odd_reconstruct gives the odd half). */
+dwf_status dwf_source_prep_sym(dwf_ctx *ctx, void *b_even, const void *phi_even,
+                               const void *phi_odd, dwf_prec prec, int nrhs,
+                               const double *mf, void *stream);
 
 /* The odd half of the solution of D psi = phi once the even half is known
  * (the second row of the even-odd system, paper eq. (dirac_equation)):

@@ -121,6 +121,8 @@ void dwf_solver_params_default(dwf_solver_params *p) {
   p->io_on_host = 0;
   p->check_every = 10;
   p->flexible = 0;
+  p->schur = 0;
+  p->inner_tol = 0.0;
 }
 
 dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device) {
@@ -266,6 +268,45 @@ dwf_status dwf_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even,
   API_CATCH(ctx)
 }
 
+dwf_status dwf_mpc_sym(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec prec,
+                       int nrhs, const double *mf, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_mpc_sym(ctx, out, in, dagger ? 1 : 0, prec, nrhs, mf, w, (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_mdagm_sym(dwf_ctx *ctx, void *out, const void *in, dwf_prec prec, int nrhs,
+                         const double *mf, void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(out && in && out != in, DWF_ERR_INVALID_ARG, "null or aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_mdagm(ctx, out, in, prec, nrhs, mf, w, nullptr, nullptr, (cudaStream_t)stream, 1);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_source_prep_sym(dwf_ctx *ctx, void *b_even, const void *phi_even,
+                               const void *phi_odd, dwf_prec prec, int nrhs, const double *mf,
+                               void *stream) {
+  API_TRY(ctx)
+  check_common(ctx, nrhs, mf);
+  check_prec_op(prec);
+  DWF_REQUIRE(b_even && phi_even && phi_odd, DWF_ERR_INVALID_ARG, "null fields");
+  DWF_REQUIRE(b_even != phi_even && b_even != phi_odd, DWF_ERR_INVALID_ARG, "aliased fields");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  dwf::OpWork w = dwf::op_work(ctx, prec, nrhs);
+  dwf::apply_source_prep_sym(ctx, b_even, phi_even, phi_odd, prec, nrhs, mf, w,
+                             (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
 dwf_status dwf_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
                                const void *phi_odd, dwf_prec prec, int nrhs, const double *mf,
                                void *stream) {
@@ -347,6 +388,9 @@ dwf_status dwf_profile_read(dwf_ctx *ctx, dwf_kernel_time *out, int cap, int *n)
 
 static void check_params(const dwf_solver_params *p) {
   DWF_REQUIRE(p != nullptr, DWF_ERR_INVALID_ARG, "null solver parameters");
+  DWF_REQUIRE(p->schur == 0 || p->schur == 1, DWF_ERR_INVALID_ARG, "schur must be 0 or 1");
+  DWF_REQUIRE(p->inner_tol >= 0.0 && p->inner_tol < 1.0, DWF_ERR_INVALID_ARG,
+              "inner_tol must be in [0, 1)");
 }
 
 dwf_status dwf_block_apply(dwf_ctx *ctx, void *out, const void *in,
@@ -361,7 +405,7 @@ dwf_status dwf_block_apply(dwf_ctx *ctx, void *out, const void *in,
   dwf::BlockPlan *bp = dwf::get_block_plan(ctx, params->block, params->inner, nrhs, st);
   dwf::BlockArgs B = dwf::block_args(ctx, bp, (char *)out, (const char *)in, nullptr, 0, nullptr);
   dwf::block_gather(bp->inner, B, nrhs, st);
-  dwf::block_apply_A(ctx, bp, params->snake, nrhs, mf, false, nullptr, st);
+  dwf::block_apply_A(ctx, bp, params->snake, nrhs, mf, false, nullptr, st, params->schur);
   dwf::block_export(bp->inner, B, bp->fAp, nrhs, st);
   API_CATCH(ctx)
 }
@@ -378,7 +422,8 @@ dwf_status dwf_block_precond(dwf_ctx *ctx, void *z, const void *r,
   cudaStream_t st = (cudaStream_t)stream;
   dwf::BlockPlan *bp = dwf::get_block_plan(ctx, params->block, params->inner, nrhs, st);
   dwf::block_precondition(ctx, bp, (char *)z, (const char *)r, params->inner_iters,
-                          params->snake, nrhs, mf, nullptr, 0, nullptr, st);
+                          params->snake, nrhs, mf, nullptr, 0, nullptr, st, DWF_FP32, nullptr,
+                          nullptr, params->inner_tol, params->schur);
   API_CATCH(ctx)
 }
 

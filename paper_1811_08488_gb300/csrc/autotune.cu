@@ -54,7 +54,7 @@ static std::string plan_key(const int block[4], dwf_prec inner) {
 std::string tune_key(const dwf_solver_params *p, int nrhs, const double *mf) {
   std::ostringstream key;
   key << p->inner << "/" << p->outer << "/" << p->inner_iters << "/" << p->snake << "/"
-      << p->tol << "/" << nrhs;
+      << p->tol << "/" << p->schur << "/" << p->inner_tol << "/" << nrhs;
   for (int r = 0; r < nrhs; ++r) key << "/" << mf[r];
   return key.str();
 }

@@ -451,8 +451,13 @@ __global__ void __launch_bounds__(kBlasThreads) blk_gather_kernel(const BlockArg
   const int grp = rhs * B.nblocks + b;
   double tot;
   if (group_reduce(acc, B.partials + (size_t)grp * gridDim.x, gridDim.x, blockIdx.x,
-                   B.counters + grp, tot))
+                   B.counters + grp, tot)) {
     B.rr[grp] = tot;
+    if (B.bstop) {
+      B.rr0[grp] = tot;
+      B.bstop[grp] = tot == 0.0 ? 1 : 0;
+    }
+  }
 }
 
 // alpha_b = rr_b / pAp_b; x += alpha p; unless LAST: r -= alpha Ap, |r|^2 -> rr_new.
@@ -462,6 +467,8 @@ __global__ void __launch_bounds__(kBlasThreads) blk_xr_kernel(const BlockArgs B)
   const int rhs = blockIdx.z, b = blockIdx.y;
   if (B.skip && B.skip[rhs]) return;
   const int grp = rhs * B.nblocks + b;
+  if (B.bstop && B.bstop[grp]) return;  // this block's residual already met the stop
+  if (B.iters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(B.iters + rhs, 1u);
   const float alpha = cta_ratio<float>(B.rr[grp], B.pAp[grp]);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);
@@ -495,8 +502,12 @@ __global__ void __launch_bounds__(kBlasThreads) blk_xr_kernel(const BlockArgs B)
     acc = cta_sum(acc, red);
     double tot;
     if (group_reduce(acc, B.partials + (size_t)grp * gridDim.x, gridDim.x, blockIdx.x,
-                     B.counters + grp, tot))
+                     B.counters + grp, tot)) {
       B.rr_new[grp] = tot;
+      // every CTA of the group has passed the check at entry: the flag
+      // takes effect from the next kernel on
+      if (B.bstop && tot <= B.tol2 * B.rr0[grp]) B.bstop[grp] = 1;
+    }
   }
 }
 
@@ -506,6 +517,7 @@ __global__ void __launch_bounds__(kBlasThreads) blk_p_kernel(const BlockArgs B) 
   const int rhs = blockIdx.z, b = blockIdx.y;
   if (B.skip && B.skip[rhs]) return;
   const int grp = rhs * B.nblocks + b;
+  if (B.bstop && B.bstop[grp]) return;
   const float beta = cta_ratio<float>(B.rr_new[grp], B.rr[grp]);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int i = (int)(idx / B.Ls), s = (int)(idx % B.Ls);

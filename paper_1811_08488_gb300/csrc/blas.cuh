@@ -46,6 +46,13 @@ struct BlockArgs {
   double *rz_out = nullptr;         // rz_out[rhs * rz_rstride]
   int rz_rstride = 0;
   const int *skip = nullptr;
+  // inner residual stop (tol2 > 0): a block stops iterating once its |r|^2
+  // fell to tol2 times its initial rr0; bstop[rhs][block] marks it, and the
+  // block operator's hops skip it
+  double tol2 = 0.0;
+  double *rr0 = nullptr;            // [rhs][nblocks]
+  int *bstop = nullptr;             // [rhs][nblocks]
+  unsigned int *iters = nullptr;    // [rhs]: block iterations done (all blocks)
 };
 
 void outer_init(dwf_prec lo, const OuterArgs &A, int nrhs, cudaStream_t st);

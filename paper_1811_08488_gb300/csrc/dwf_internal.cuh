@@ -171,6 +171,7 @@ struct HopParams {
   int dot_rstride = 0;
   unsigned int *counters = nullptr;  // [rhs][block]
   const int *skip = nullptr;    // per rhs: nonzero = skip (converged)
+  const int *bskip = nullptr;   // per (rhs, block): nonzero = skip (inner stop met)
   KernProf *prof = nullptr;     // timer slot of this launch (null: profiling off)
   unsigned long long alg_bytes = 0;  // compulsory bytes of this launch
   LsCoef coef[kMaxRhs];
@@ -303,7 +304,7 @@ void launch_m5inv_gemm(dwf_ctx *ctx, dwf_prec p, char *out, const char *in, int 
                        const double *mf, cudaStream_t st);
 void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride,
                   int nsite, int Ls, int dagger, int inv, int nrhs, const LsCoef *coef,
-                  cudaStream_t st);
+                  cudaStream_t st, int coef_div = 1);
 
 // fields.cu: layout and precision conversions
 void launch_import(dwf_prec p, char *native, long long nstride, const void *canon,

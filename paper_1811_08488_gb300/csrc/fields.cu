@@ -9,13 +9,18 @@ namespace dwf {
 // ---------------------------------------------------------------------------
 // Standalone Ls-direction operator: out = q0 (p0 + p1 S)[(1 - r S)^-1] in.
 // ---------------------------------------------------------------------------
+// Grid z runs over nrhs * coef_div fields of nsite sites (block-local fields
+// of every block are laid out like right-hand sides); field z uses the
+// coefficients of right-hand side z / coef_div. A CTA reads its sites before it
+// writes them, so out may equal in.
 template <class S, bool DAG>
 __global__ void __launch_bounds__(256) ls_kernel(char *out, const char *in, long long rstride,
                                                  long long soff, int nsite, int Ls, int inv,
-                                                 const __grid_constant__ HopParams P) {
+                                                 int coef_div, const __grid_constant__ HopParams P) {
   using R = typename S::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rhs = blockIdx.z;
+  const LsCoef &cf = P.coef[rhs / coef_div];
   const int nsites = P.nsites;
   const int tid = threadIdx.x, s = tid % Ls, sl = tid / Ls;
   const int site = blockIdx.x * nsites + sl;
@@ -34,7 +39,7 @@ __global__ void __launch_bounds__(256) ls_kernel(char *out, const char *in, long
   for (int w = tid; w < nsites * 24; w += blockDim.x) {
     if (blockIdx.x * nsites + w / 24 >= nsite) continue;
     const bool down = ((w % 24) < 12) != DAG;
-    ls_column<R>(T + w * col, nullptr, Ls, down, inv != 0, kc<R>(P.coef[rhs]));
+    ls_column<R>(T + w * col, nullptr, Ls, down, inv != 0, kc<R>(cf));
   }
   __syncthreads();
   if (active) {
@@ -46,7 +51,8 @@ __global__ void __launch_bounds__(256) ls_kernel(char *out, const char *in, long
 }
 
 void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride, int nsite, int Ls,
-                  int dagger, int inv, int nrhs, const LsCoef *coef, cudaStream_t st) {
+                  int dagger, int inv, int nrhs, const LsCoef *coef, cudaStream_t st,
+                  int coef_div) {
   HopParams P;
   for (int r = 0; r < nrhs; ++r) {
     P.coef[r] = coef[r];
@@ -54,21 +60,20 @@ void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride, int 
   }
   const int nsites = hop_sites_per_cta(Ls, p);
   P.nsites = nsites;
-  dim3 grid((nsite + nsites - 1) / nsites, 1, nrhs), block((nsites * Ls + 31) / 32 * 32);
+  dim3 grid((nsite + nsites - 1) / nsites, 1, nrhs * coef_div), block((nsites * Ls + 31) / 32 * 32);
+  // at most about 37 KB (nsites * Ls is at most 256): no opt-in beyond 48 KB
   const size_t smem = (size_t)nsites * 24 * (Ls + 1) * (p == DWF_FP64 ? 8 : 4);
   const long long soff = (long long)align_up(field_data_bytes(p, nsite, Ls), 256);
-#define LSK(ST, D)                                                                          \
-  do {                                                                                      \
-    DWF_CUDA_TRY(cudaFuncSetAttribute(ls_kernel<ST, D>,                                     \
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10)); \
-    ls_kernel<ST, D><<<grid, block, smem, st>>>(out, in, rstride, soff, nsite, Ls, inv, P); \
-  } while (0)
+#define LSK(ST, D) \
+  ls_kernel<ST, D><<<grid, block, smem, st>>>(out, in, rstride, soff, nsite, Ls, inv, coef_div, P)
   if (p == DWF_FP64) {
     if (dagger) LSK(F64, true); else LSK(F64, false);
   } else if (p == DWF_FP32) {
     if (dagger) LSK(F32, true); else LSK(F32, false);
+  } else if (p == DWF_FP16) {
+    if (dagger) LSK(F16, true); else LSK(F16, false);
   } else {
-    throw Error{DWF_ERR_UNSUPPORTED, "M_5 / M_5^-1 entry points take FP64 or FP32 fields"};
+    if (dagger) LSK(BF16, true); else LSK(BF16, false);
   }
 #undef LSK
   DWF_CUDA_TRY(cudaGetLastError());

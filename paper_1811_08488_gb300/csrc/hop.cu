@@ -258,6 +258,7 @@ __device__ __forceinline__ void hop_body(const HopParams &P) {
   __shared__ double red[32];
   const int rhs = blockIdx.z, blk = blockIdx.y;
   if (P.skip && P.skip[rhs]) return;
+  if (P.bskip && P.bskip[rhs * P.nblocks + blk]) return;
   const int Ls = P.Ls;
   const int nsites = P.nsites;  // blockDim.x is nsites * Ls rounded up to whole warps
   const int tid = threadIdx.x;
@@ -569,6 +570,7 @@ __device__ __forceinline__ void hop2_body(const HopParams &P) {
   __shared__ double red[32];
   const int rhs = blockIdx.z, blk = blockIdx.y;
   if (P.skip && P.skip[rhs]) return;
+  if (P.bskip && P.bskip[rhs * P.nblocks + blk]) return;
   const int Ls = P.Ls, np = Ls >> 1;
   const int nsites = P.nsites;  // blockDim.x is nsites * Ls / 2 rounded up to whole warps
   const int tid = threadIdx.x;

@@ -124,18 +124,24 @@ static void mpc_first(dwf_ctx *ctx, void *odd_out, const void *in, int dagger, d
 }
 
 // Second half: out(even) = M_5 in + 1/2 Dhop u, or M_5^+ in + 1/2 M_phi^+ Dhop^+ v.
+// The symmetric form (schur = 1): out = in + M_5^-1 (1/2 Dhop u), or
+// in + 1/2 M_phi^+ Dhop^+ v.
 static void mpc_second(dwf_ctx *ctx, void *out, const void *odd_in, const void *in, int dagger,
                        dwf_prec p, int nrhs, const double *mf, const DotSpec *dot,
-                       const int *skip, cudaStream_t st) {
+                       const int *skip, cudaStream_t st, int schur = 0) {
   HopParams P = global_params(ctx, p, 0, odd_in, out);
   P.xown = global_ref(ctx, p, in);
   const dwf_action &a = ctx->act;
   for (int r = 0; r < nrhs; ++r) {
-    P.coef[r] = dagger ? coef_mphi(a, mf[r], 0.5) : coef_identity(0.5);
+    if (schur && !dagger)
+      P.coef[r] = coef_m5inv(a, mf[r], 0.5);
+    else
+      P.coef[r] = dagger ? coef_mphi(a, mf[r], 0.5) : coef_identity(0.5);
     P.coef[r].mf = mf[r];
-    P.coef[r].a0 = alpha_of(a);
-    P.coef[r].a1 = beta_of(a);
+    P.coef[r].a0 = schur ? 1.0 : alpha_of(a);
+    P.coef[r].a1 = schur ? 0.0 : beta_of(a);
   }
+  P.inv = (schur && !dagger) ? 1 : 0;
   P.epi = 1;
   P.has_x = 1;
   P.skip = skip;
@@ -155,6 +161,62 @@ void apply_mpc(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, 
   char *odd = dagger ? w.v : w.u;
   mpc_first(ctx, odd, in, dagger, p, nrhs, mf, nullptr, st);
   mpc_second(ctx, out, odd, in, dagger, p, nrhs, mf, nullptr, nullptr, st);
+}
+
+// out = M_5^-1 in or M_5^-+ in on even fields (one Ls pass).
+static void m5inv_pass(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
+                       const double *mf, cudaStream_t st) {
+  LsCoef c[kMaxRhs];
+  for (int r = 0; r < nrhs; ++r) c[r] = coef_m5inv(ctx->act, mf[r], 1.0);
+  launch_ls_op(p, static_cast<char *>(out), static_cast<const char *>(in),
+               (long long)field_rhs_bytes(p, ctx->geo.Vh, ctx->act.Ls), ctx->geo.Vh, ctx->act.Ls,
+               dagger, 1, nrhs, c, st);
+}
+
+// D_sym in = in - M_5^-1 M^4_eo M_5^-1 M^4_oe in (odd temporary odd_tmp), or
+// D_sym^+ in = in - (M^4_oe)^+ M_5^-+ (M^4_eo)^+ M_5^-+ in (with the even
+// temporary even_tmp for M_5^-+ in as well).
+static void mpc_sym(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
+                    const double *mf, char *odd_tmp, char *even_tmp, const DotSpec *dot,
+                    const int *skip, cudaStream_t st) {
+  const void *hop_in = in;
+  if (dagger) {
+    m5inv_pass(ctx, even_tmp, in, 1, p, nrhs, mf, st);
+    hop_in = even_tmp;
+  }
+  mpc_first(ctx, odd_tmp, hop_in, dagger, p, nrhs, mf, skip, st);
+  mpc_second(ctx, out, odd_tmp, in, dagger, p, nrhs, mf, dot, skip, st, 1);
+}
+
+void apply_mpc_sym(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
+                   const double *mf, const OpWork &w, cudaStream_t st) {
+  mpc_sym(ctx, out, in, dagger, p, nrhs, mf, w.u, w.v, nullptr, nullptr, st);
+}
+
+// b = D_sym^+ M_5^-1 phi_hat_e: the right-hand side of the symmetric form's
+// normal equation for D psi = phi.
+void apply_source_prep_sym(dwf_ctx *ctx, void *b_even, const void *phi_even, const void *phi_odd,
+                           dwf_prec p, int nrhs, const double *mf, const OpWork &w,
+                           cudaStream_t st) {
+  // phi_hat_e -> w.y (w.u is used on the way)
+  const int Vh = ctx->geo.Vh, Ls = ctx->act.Ls;
+  LsCoef c[kMaxRhs];
+  for (int r = 0; r < nrhs; ++r) c[r] = coef_k(ctx->act, mf[r], 1.0);
+  launch_ls_op(p, w.u, static_cast<const char *>(phi_odd), (long long)field_rhs_bytes(p, Vh, Ls),
+               Vh, Ls, 0, 1, nrhs, c, st);
+  HopParams P = global_params(ctx, p, 0, w.u, w.y);
+  P.xown = global_ref(ctx, p, phi_even);
+  for (int r = 0; r < nrhs; ++r) {
+    P.coef[r] = coef_identity(0.5);
+    P.coef[r].mf = mf[r];
+    P.coef[r].a0 = 1.0;
+    P.coef[r].a1 = 0.0;
+  }
+  P.epi = 1;
+  P.has_x = 1;
+  launch(ctx, p, P, 0, 0, nrhs, st);
+  m5inv_pass(ctx, w.v, w.y, 0, p, nrhs, mf, st);       // q = M_5^-1 phi_hat_e
+  mpc_sym(ctx, b_even, w.v, 1, p, nrhs, mf, w.u, w.y, nullptr, nullptr, st);
 }
 
 // Right-hand side of the normal equation for the full system D psi = phi
@@ -209,7 +271,18 @@ void apply_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
 
 void apply_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec p, int nrhs,
                  const double *mf, const OpWork &w, const DotSpec *dot, const int *skip,
-                 cudaStream_t st) {
+                 cudaStream_t st, int schur) {
+  if (schur) {
+    // D_sym^+ D_sym: y = D_sym in, then D_sym^+ y with the dot against in
+    DotSpec d;
+    if (dot) {
+      d = *dot;
+      d.dotv = static_cast<const char *>(in);
+    }
+    mpc_sym(ctx, w.y, in, 0, p, nrhs, mf, w.u, nullptr, nullptr, skip, st);
+    mpc_sym(ctx, out, w.y, 1, p, nrhs, mf, w.u, w.v, dot ? &d : nullptr, skip, st);
+    return;
+  }
   mpc_first(ctx, w.u, in, 0, p, nrhs, mf, skip, st);
   mpc_second(ctx, w.y, w.u, in, 0, p, nrhs, mf, nullptr, skip, st);
   mpc_first(ctx, w.v, w.y, 1, p, nrhs, mf, skip, st);
@@ -291,7 +364,12 @@ BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int 
     alloc(bp->u1, bp->fu1, inner, g.n_o1);
     alloc(bp->u2, bp->fu2, inner, g.n_o1);
     alloc(bp->y, bp->fy, inner, g.n_e2);
-    bp->scal.ensure(sizeof(double) * 3 * nrhs * nb + 64);
+    alloc(bp->w2, bp->fw2, inner, g.n_e2);
+    bp->scal.ensure(sizeof(double) * 5 * nrhs * nb + 64);
+    bp->bstop.ensure(sizeof(int) * nrhs * nb);
+    DWF_CUDA_TRY(cudaMemset(bp->bstop.p, 0, bp->bstop.bytes));
+    bp->iters.ensure(sizeof(unsigned int) * nrhs);
+    DWF_CUDA_TRY(cudaMemset(bp->iters.p, 0, bp->iters.bytes));
     const int sites = hop_sites_per_cta(Ls, inner);
     const int tiles = std::max((g.n_b + sites - 1) / sites, block_tiles(g.n_b, Ls));
     bp->partials.ensure(sizeof(double) * (size_t)nrhs * nb * tiles);
@@ -313,7 +391,7 @@ BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int 
 // 2 (n_e2), the odd intermediates within distance 1 (n_o1). With snake = 0
 // every hop is restricted to the block instead (the truncated operator).
 void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const double *mf,
-                   bool with_dot, const int *skip, cudaStream_t st) {
+                   bool with_dot, const int *skip, cudaStream_t st, int schur) {
   const BlockGeometry &g = bp->bg;
   const dwf_action &a = ctx->act;
   HopParams base;
@@ -324,6 +402,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   base.Ls = bp->Ls;
   base.nblocks = g.nblocks;
   base.skip = skip;
+  base.bskip = bp->stop_active ? bp->bstop.as<int>() : nullptr;
   base.epi = 1;
   base.role = 1;
   const int odd_out = snake ? g.n_o1 : g.n_ob;
@@ -346,7 +425,8 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   }
   launch(ctx, bp->inner, P, 0, 1, nrhs, st);
 
-  // hop 2: even (distance <= 2) <- odd; y = M_5 p + 1/2 Dhop u1  (= D_PC P_s p)
+  // hop 2: even (distance <= 2) <- odd; y = M_5 p + 1/2 Dhop u1  (= D_PC P_s p),
+  // or y = p + M_5^-1 (1/2 Dhop u1) (= D_sym P_s p)
   P = base;
   P.in = bp->fu1;
   P.out = bp->fy;
@@ -359,16 +439,27 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   P.xown = bp->fp;
   P.xown_limit = g.n_b;
   for (int r = 0; r < nrhs; ++r) {
-    P.coef[r] = coef_identity(0.5);
+    P.coef[r] = schur ? coef_m5inv(a, mf[r], 0.5) : coef_identity(0.5);
     P.coef[r].mf = mf[r];
-    P.coef[r].a0 = alpha_of(a);
-    P.coef[r].a1 = beta_of(a);
+    P.coef[r].a0 = schur ? 1.0 : alpha_of(a);
+    P.coef[r].a1 = schur ? 0.0 : beta_of(a);
   }
+  P.inv = schur ? 1 : 0;
   launch(ctx, bp->inner, P, 0, 0, nrhs, st);
 
+  // symmetric form: w = M_5^-+ y on the even distance-2 region of every block
+  // (one Ls pass over the block-local fields, blocks taken as right-hand sides)
+  if (schur) {
+    LsCoef c[kMaxRhs];
+    for (int r = 0; r < nrhs; ++r) c[r] = coef_m5inv(a, mf[r], 1.0);
+    launch_ls_op(bp->inner, bp->w2.c(), bp->y.c(), bp->fy.bstride, even_mid, bp->Ls, 1, 1, nrhs,
+                 c, st, g.nblocks);
+  }
+
   // hop 3: odd (distance <= 1) <- even (distance <= 2); u2 = K^+ (-1/2 Dhop^+ y)
+  // (y replaced by w in the symmetric form)
   P = base;
-  P.in = bp->fy;
+  P.in = schur ? bp->fw2 : bp->fy;
   P.out = bp->fu2;
   P.nbr = bp->nbr_oe.as<int>();
   P.n_out = odd_out;
@@ -380,6 +471,7 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   launch(ctx, bp->inner, P, 1, 0, nrhs, st);
 
   // hop 4: even block sites <- odd; Ap = M_5^+ y + 1/2 M_phi^+ Dhop^+ u2
+  // (y + 1/2 M_phi^+ Dhop^+ u2 in the symmetric form)
   P = base;
   P.in = bp->fu2;
   P.out = bp->fAp;
@@ -393,8 +485,8 @@ void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const doubl
   P.xown_limit = g.n_b;
   for (int r = 0; r < nrhs; ++r) {
     P.coef[r] = coef_mphi(a, mf[r], 0.5);
-    P.coef[r].a0 = alpha_of(a);
-    P.coef[r].a1 = beta_of(a);
+    P.coef[r].a0 = schur ? 1.0 : alpha_of(a);
+    P.coef[r].a1 = schur ? 0.0 : beta_of(a);
   }
   if (with_dot) {
     P.dot = 1;
@@ -440,6 +532,8 @@ BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double
   B.rz_out = rz_out ? rz_out : sc + 3 * n;  // scratch slot when unused
   B.rz_rstride = rz_out ? rz_rstride : 0;
   B.skip = skip;
+  B.rr0 = sc + 4 * n;
+  B.iters = bp->iters.as<unsigned int>();
   return B;
 }
 
@@ -448,20 +542,28 @@ BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double
 void block_precondition(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, int k, int snake,
                         int nrhs, const double *mf, double *rz_out, int rz_rstride,
                         const int *skip, cudaStream_t st, dwf_prec glob, const char *ap,
-                        double *apz_out) {
+                        double *apz_out, double inner_tol, int schur) {
   BlockArgs B = block_args(ctx, bp, z, r, rz_out, rz_rstride, skip, glob);
   if (ap && apz_out) {
     B.apglob = ap;
     B.apz_out = apz_out;
   }
+  // inner residual stop: a block stops once |r_s| <= inner_tol |r_s(0)| (at
+  // most k iterations); its later launches return at entry
+  bp->stop_active = inner_tol > 0.0;
+  if (bp->stop_active) {
+    B.tol2 = inner_tol * inner_tol;
+    B.bstop = bp->bstop.as<int>();
+  }
   block_gather(bp->inner, B, nrhs, st);
   for (int it = 0; it < k; ++it) {
-    block_apply_A(ctx, bp, snake, nrhs, mf, true, skip, st);
+    block_apply_A(ctx, bp, snake, nrhs, mf, true, skip, st, schur);
     const int last = it == k - 1;
     block_xr(bp->inner, B, last, nrhs, st);
     if (!last) block_p(bp->inner, B, nrhs, st);
   }
   block_scatter(B, nrhs, st);
+  bp->stop_active = false;
 }
 
 // ---------------------------------------------------------------------------
@@ -549,14 +651,16 @@ static void enqueue_iteration(SolveSetup &S, cudaStream_t st) {
   const int *skip = sp->skip_iter.as<int>();
   OuterArgs A = S.A;
   A.skip = skip;
-  apply_mdagm(S.ctx, sp->Ap.p, sp->p.p, sp->lo, S.nrhs, S.mf, S.wlo, &S.dot, skip, st);
+  apply_mdagm(S.ctx, sp->Ap.p, sp->p.p, sp->lo, S.nrhs, S.mf, S.wlo, &S.dot, skip, st,
+              S.prm->schur);
   outer_axpy_xr(sp->lo, A, S.nrhs, st);
   if (!A.plain)
     block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
                        S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
                        (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo,
                        A.flexible ? sp->Ap.c() : nullptr,
-                       A.flexible ? &sp->scal.as<OuterScalars>()->apz : nullptr);
+                       A.flexible ? &sp->scal.as<OuterScalars>()->apz : nullptr,
+                       S.prm->inner_tol, S.prm->schur);
   outer_xpay_p(sp->lo, A, S.nrhs, st);
 }
 
@@ -568,12 +672,14 @@ static void enqueue_reliable_update(SolveSetup &S, cudaStream_t st) {
   OuterArgs A = S.A;
   A.skip = skip;
   outer_promote(sp->lo, A, S.nrhs, st);
-  apply_mdagm(S.ctx, sp->Ax64.p, sp->x64.p, DWF_FP64, S.nrhs, S.mf, S.w64, nullptr, skip, st);
+  apply_mdagm(S.ctx, sp->Ax64.p, sp->x64.p, DWF_FP64, S.nrhs, S.mf, S.w64, nullptr, skip, st,
+              S.prm->schur);
   outer_ru_residual(sp->lo, A, S.nrhs, st);
   if (!A.plain) {
     block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
                        S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo);
+                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo, nullptr,
+                       nullptr, S.prm->inner_tol, S.prm->schur);
     outer_set_rz(A, S.nrhs, st);
   }
 }
@@ -739,11 +845,13 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
                                st));
   DWF_CUDA_TRY(cudaMemsetAsync(sp->x64.p, 0, sp->x64.bytes, st));
   DWF_CUDA_TRY(cudaMemsetAsync(sp->xlo.p, 0, sp->xlo.bytes, st));
+  if (bp) DWF_CUDA_TRY(cudaMemsetAsync(bp->iters.p, 0, bp->iters.bytes, st));
   outer_init(lo, A, nrhs, st);
   if (!plain) {
     block_precondition(ctx, bp, sp->z.c(), sp->rlo.c(), prm->inner_iters, prm->snake, nrhs, mf,
                        &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), nullptr, st, lo);
+                       (int)(sizeof(OuterScalars) / sizeof(double)), nullptr, st, lo, nullptr,
+                       nullptr, prm->inner_tol, prm->schur);
     outer_set_rz(A, nrhs, st);
   }
   outer_copy_p(lo, A, nrhs, st);
@@ -949,11 +1057,17 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   const double dslash_gbs = (ctx->prof_on && hop_ns1 > hop_ns0)
                                 ? (hop_bytes1 - hop_bytes0) / (hop_ns1 - hop_ns0)
                                 : -1.0;
+  // inner CG iterations, counted on the device over all blocks (fewer than
+  // outer_iters * k per block when the inner residual stop is on)
+  std::vector<unsigned int> blk_iters(nrhs, 0);
+  if (bp)
+    DWF_CUDA_TRY(cudaMemcpy(blk_iters.data(), bp->iters.p, sizeof(unsigned int) * nrhs,
+                            cudaMemcpyDeviceToHost));
   bool all_conv = true;
   for (int r = 0; r < nrhs; ++r) {
     if (info) {
       info[r].outer_iters = sp->host_scal[r].iter;
-      info[r].inner_iters_total = sp->host_scal[r].iter * (plain ? 0 : prm->inner_iters);
+      info[r].inner_iters_total = bp ? (int)(blk_iters[r] / (unsigned)bp->bg.nblocks) : 0;
       info[r].reliable_updates = nru[r];
       info[r].converged = final_res[r] >= 0 && final_res[r] <= prm->tol;
       info[r].true_resid = final_res[r];

@@ -34,9 +34,15 @@ void apply_source_prep(dwf_ctx *ctx, void *b_even, const void *phi_even, const v
 void apply_odd_reconstruct(dwf_ctx *ctx, void *psi_odd, const void *psi_even,
                            const void *phi_odd, dwf_prec p, int nrhs, const double *mf,
                            const OpWork &w, cudaStream_t st);
+// schur = 0: A = D_PC^+ D_PC; 1: A_sym = D_sym^+ D_sym (symmetric form)
 void apply_mdagm(dwf_ctx *ctx, void *out, const void *in, dwf_prec p, int nrhs,
                  const double *mf, const OpWork &w, const DotSpec *dot, const int *skip,
-                 cudaStream_t st);
+                 cudaStream_t st, int schur = 0);
+void apply_mpc_sym(dwf_ctx *ctx, void *out, const void *in, int dagger, dwf_prec p, int nrhs,
+                   const double *mf, const OpWork &w, cudaStream_t st);
+void apply_source_prep_sym(dwf_ctx *ctx, void *b_even, const void *phi_even, const void *phi_odd,
+                           dwf_prec p, int nrhs, const double *mf, const OpWork &w,
+                           cudaStream_t st);
 
 // The multisplitting block plan: geometry, tables, per-block links, vectors.
 struct BlockPlan {
@@ -47,25 +53,30 @@ struct BlockPlan {
   DevBuf nbr_oe, nbr_eo, gmap_b, gowner;
   DevBuf links;
   long long link_bstride = 0;
-  DevBuf r, p, Ap, x, u1, y, u2;
-  FieldRef fr, fp, fAp, fx, fu1, fy, fu2;
-  DevBuf scal;  // rr, rr_new, pAp: 3 x [nrhs][nblocks] doubles
+  DevBuf r, p, Ap, x, u1, y, u2, w2;
+  FieldRef fr, fp, fAp, fx, fu1, fy, fu2, fw2;  // w2: M_5^-+ y (symmetric form)
+  DevBuf scal;  // rr, rr_new, pAp, (scratch), rr0: 5 x [nrhs][nblocks] doubles
   DevBuf partials, counters, gpart, gcount, gpart2, gcount2;
+  DevBuf bstop;  // [nrhs][nblocks] inner residual stop flags
+  DevBuf iters;  // [nrhs] block iterations counted by the inner CG
   bool links_valid = false;
+  bool stop_active = false;  // the inner residual stop is on for the launches being built
 };
 
 BlockPlan *get_block_plan(dwf_ctx *ctx, const int block[4], dwf_prec inner, int nrhs,
                           cudaStream_t st);
-// out = (+)_s A_s p on the plan's block vectors (p -> Ap), optional <p, Ap>.
+// out = (+)_s A_s p on the plan's block vectors (p -> Ap), optional <p, Ap>;
+// schur = 1: the blocks of the symmetric form's normal operator.
 void block_apply_A(dwf_ctx *ctx, BlockPlan *bp, int snake, int nrhs, const double *mf,
-                   bool with_dot, const int *skip, cudaStream_t st);
+                   bool with_dot, const int *skip, cudaStream_t st, int schur = 0);
 // z = M^-1 r on FP32 global fields; <r, z> -> rz_out[rhs * rz_rstride] if given.
 // glob: precision of z and r (FP32, or FP64 for an FP64 outer solver). With
 // ap and apz_out, also <A p, z> -> apz_out[rhs * rz_rstride] (flexible PCG).
 void block_precondition(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, int k, int snake,
                         int nrhs, const double *mf, double *rz_out, int rz_rstride,
                         const int *skip, cudaStream_t st, dwf_prec glob = DWF_FP32,
-                        const char *ap = nullptr, double *apz_out = nullptr);
+                        const char *ap = nullptr, double *apz_out = nullptr,
+                        double inner_tol = 0.0, int schur = 0);
 
 BlockArgs block_args(dwf_ctx *ctx, BlockPlan *bp, char *z, const char *r, double *rz_out,
                      int rz_rstride, const int *skip, dwf_prec glob = DWF_FP32);

@@ -31,6 +31,7 @@ EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_def
            "dwf_dslash_eo", "dwf_m5", "dwf_m5inv", "dwf_m5inv_gemm", "dwf_mpc", "dwf_mdagm", "dwf_mdagm_noalloc",
            "dwf_block_apply",
            "dwf_block_precond", "dwf_autotune_block", "dwf_source_prep", "dwf_odd_reconstruct",
+           "dwf_mpc_sym", "dwf_mdagm_sym", "dwf_source_prep_sym",
            "mspcg_solve", "dwf_profile_enable", "dwf_profile_read"]
 
 
@@ -49,7 +50,8 @@ class SolverParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("inner_iters", C.c_int),
                 ("block", C.c_int * 4), ("outer", C.c_int), ("inner", C.c_int),
                 ("delta", C.c_double), ("snake", C.c_int), ("use_graph", C.c_int),
-                ("io_on_host", C.c_int), ("check_every", C.c_int), ("flexible", C.c_int)]
+                ("io_on_host", C.c_int), ("check_every", C.c_int), ("flexible", C.c_int),
+                ("schur", C.c_int), ("inner_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -94,6 +96,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_mdagm": (I, [P, P, P, I, I, D, P]),
         "dwf_mdagm_noalloc": (I, [P, P, P, I, I, D, P]),
         "dwf_source_prep": (I, [P, P, P, P, I, I, D, P]),
+        "dwf_source_prep_sym": (I, [P, P, P, P, I, I, D, P]),
+        "dwf_mpc_sym": (I, [P, P, P, I, I, I, D, P]),
+        "dwf_mdagm_sym": (I, [P, P, P, I, I, D, P]),
         "dwf_odd_reconstruct": (I, [P, P, P, P, I, I, D, P]),
         "dwf_block_apply": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "dwf_block_precond": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
@@ -250,6 +255,19 @@ class Context:
         self._check(lib().dwf_mpc(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)), int(dagger),
                                   PREC.get(prec, prec), m.size, mp, _stream(stream)))
 
+    def mpc_sym(self, out, inp, dagger, prec, mf, stream=None):
+        """dwf_mpc_sym: D_sym = 1 - M_5^-1 M^4_eo M_5^-1 M^4_oe (or its adjoint)."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_mpc_sym(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
+                                      int(dagger), PREC.get(prec, prec), m.size, mp,
+                                      _stream(stream)))
+
+    def mdagm_sym(self, out, inp, prec, mf, stream=None):
+        """dwf_mdagm_sym: D_sym^+ D_sym."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_mdagm_sym(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
+                                        PREC.get(prec, prec), m.size, mp, _stream(stream)))
+
     def mdagm(self, out, inp, prec, mf, stream=None):
         m, mp = _masses(mf)
         self._check(lib().dwf_mdagm(self._h, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(inp)),
@@ -280,6 +298,14 @@ class Context:
                                           C.c_void_p(_ptr(phi_even)), C.c_void_p(_ptr(phi_odd)),
                                           PREC.get(prec, prec), m.size, mp, _stream(stream)))
 
+    def source_prep_sym(self, b_even, phi_even, phi_odd, prec, mf, stream=None):
+        """dwf_source_prep_sym: b = D_sym^+ M_5^-1 (phi_e - M^4_eo M_5^-1 phi_o)."""
+        m, mp = _masses(mf)
+        self._check(lib().dwf_source_prep_sym(self._h, C.c_void_p(_ptr(b_even)),
+                                              C.c_void_p(_ptr(phi_even)),
+                                              C.c_void_p(_ptr(phi_odd)), PREC.get(prec, prec),
+                                              m.size, mp, _stream(stream)))
+
     def odd_reconstruct(self, psi_odd, psi_even, phi_odd, prec, mf, stream=None):
         """dwf_odd_reconstruct: psi_o = M_5^-1 (phi_o - M^4_oe psi_e), native fields."""
         m, mp = _masses(mf)
@@ -292,14 +318,16 @@ class Context:
         """Solve D psi = phi: source preparation, mspcg_solve on the normal
         equation, odd reconstruction. phi_even / phi_odd: canonical complex128
         device tensors [nrhs][...]; returns (psi_even, psi_odd, status, infos)
-        in the same layout. Every step runs in the library's kernels."""
+        in the same layout. params.schur selects the normal equation (and its
+        right-hand side). Every step runs in the library's kernels."""
         import torch
         m, _ = _masses(mf)
         nrhs = m.size
         nat = {k: self.new_field("fp64", nrhs) for k in ("pe", "po", "b", "xe", "xo")}
         self.field_import(nat["pe"], "fp64", phi_even, nrhs)
         self.field_import(nat["po"], "fp64", phi_odd, nrhs)
-        self.source_prep(nat["b"], nat["pe"], nat["po"], "fp64", list(m), stream)
+        prep = self.source_prep_sym if params.schur else self.source_prep
+        prep(nat["b"], nat["pe"], nat["po"], "fp64", list(m), stream)
         b = torch.zeros_like(phi_even)
         self.field_export(b, nat["b"], "fp64", nrhs)
         psi_e = torch.zeros_like(phi_even)

@@ -95,15 +95,22 @@ def test_multi_rhs_uneven_masses():
                                 dict(inner_iters=4, block=(4, 4, 4, 4), inner="fp16")])
 def test_device_decided_early_exit_uneven_iteration_counts(kw):
     """Four right-hand sides in one call whose outer-iteration counts differ by
-    more than 2x (m_f 0.005 to 1.0, and a zero source that x = 0 solves): the
-    device decides every right-hand side's reliable updates and convergence
-    after each iteration and skips the finished ones, the host waits once per
-    graph launch, and every right-hand side meets the oracle's FP64 residual
-    bound. The host-driven loop (use_graph = 0) reaches the same bound with
-    more host waits."""
+    more than 2x: Gaussian sources at m_f 0.005 and 0.1, a source A^6 g whose
+    low modes are suppressed (so CG needs far fewer iterations to reach the
+    same relative residual) and a zero source that x = 0 solves. The device
+    decides every right-hand side's reliable updates and convergence after
+    each iteration and skips the finished ones, the host waits once per graph
+    launch, and every right-hand side meets the oracle's FP64 residual bound.
+    The host-driven loop (use_graph = 0) reaches the same bound with more host
+    waits."""
     act, Uc, U, ctx = setup((8, 8, 8, 8), 8, 1.5, 0.5, 0.4, 1006)
     masses = [0.005, 0.1, 1.0, 0.02]
     srcs = [syn.half_field(act.dims, act.Ls, 2006 + r) for r in range(3)]
+    smooth = op.half_to_full(srcs[2], 0)
+    for _ in range(6):
+        smooth = op.mdagm(act, U, smooth, masses[2])
+        smooth /= np.sqrt(op.norm2(smooth))
+    srcs[2] = op.full_to_half(smooth, 0)
     srcs.append(np.zeros_like(srcs[0]))
     st, info, x = run(ctx, srcs, masses, tol=1e-10, **kw)
     assert st == 0
