@@ -52,6 +52,13 @@ static inline int dist1(int u, int bl, int L) {
   return std::min(u - bl + 1, L - u);
 }
 
+// Which side of the block interval u lies on: 0 inside, 1 above (u >= bl),
+// 2 below (wrapped round, nearer the block's start).
+static inline int side1(int u, int bl, int L) {
+  if (u < bl) return 0;
+  return (u - bl + 1 <= L - u) ? 1 : 2;
+}
+
 void build_block_geometry(BlockGeometry &bg, const int dims[4], const int block[4]) {
   int nb[4];
   for (int m = 0; m < 4; ++m) {
@@ -75,6 +82,7 @@ void build_block_geometry(BlockGeometry &bg, const int dims[4], const int block[
   struct Site {
     int u[4];
     int d, par, lexl;
+    int face;  // side1 of the four coordinates, two bits each
   };
   std::vector<Site> sites;
   for (int t : cand[3])
@@ -88,6 +96,8 @@ void build_block_geometry(BlockGeometry &bg, const int dims[4], const int block[
           if (s.d > 2) continue;
           s.par = (x + y + z + t) & 1;
           s.lexl = lex(s.u, dims);
+          s.face = 0;
+          for (int m = 0; m < 4; ++m) s.face |= side1(s.u[m], block[m], dims[m]) << (2 * m);
           sites.push_back(s);
         }
   std::vector<Site> ev, od;
@@ -95,8 +105,12 @@ void build_block_geometry(BlockGeometry &bg, const int dims[4], const int block[
     if (s.par == 0) ev.push_back(s);
     else if (s.d <= 1) od.push_back(s);
   }
+  // by distance (the block's own sites first, then the rings), and within a
+  // ring by face, so that the sites of one warp share their pattern of
+  // neighbours inside the region (a ring site has only one or two)
   auto key = [](const Site &a, const Site &b) {
     if (a.d != b.d) return a.d < b.d;
+    if (a.face != b.face) return a.face < b.face;
     return a.lexl < b.lexl;
   };
   std::sort(ev.begin(), ev.end(), key);

@@ -2,11 +2,17 @@
 // operator application of the solver (paper Sec. 2.2, M^4 = D^w M_phi and
 // eq. for D^w; Sec. 2.3 for its use inside the Dirichlet block operator).
 //
-// One thread computes one output (site, s). A CTA holds SITES sites x all Ls
-// slices, so the links of a site are loaded once per CTA line and broadcast to
-// the Ls threads of the site, and the Ls-direction operators that follow the
-// hop (M_phi^+, M_5^-1 M_phi, M_5) run in shared memory on the CTA's own sites
-// (one thread per site and spin-colour component walks s).
+// Two kernels. hop2_kernel (FP32/FP16/BF16 fields, even Ls): one thread per
+// pair of slices (s0, s0 + 1) of one output site; the Ls/2 threads of a site
+// are consecutive lanes of one warp (a warp holds whole sites), so the links
+// of a site are loaded once per warp line, and everything that couples
+// neighbouring slices -- M_phi on load (s0 - 1, s0 + 2), the Ls epilogue
+// (M_phi^+, M_5^-1, K = M_phi M_5^-1 and their adjoints) and the x-term of the
+// epilogue -- is exchanged between those lanes with warp shuffles; the
+// epilogue's (1 - r S)^-1 is a scan over the site's lanes. It uses no shared
+// memory outside its reductions, so the unified L1 serves the neighbour
+// gather. hop_kernel (FP64 fields, odd Ls): one thread per output (site, s),
+// the Ls epilogue walks columns in shared memory.
 //
 // For output site x and direction mu (chiral basis, g_mu = [[0, A],[A^+, 0]]):
 //   forward : (1 - sg g_mu) U_mu(x)      chi(x+mu)
@@ -458,63 +464,86 @@ __device__ __forceinline__ void proj_mul_acc2(float2 *acc, const float2 *v, cons
   }
 }
 
+// Lanes of one site: the np = Ls/2 thread pairs of a site are consecutive lanes
+// of one warp (sites never straddle a warp), so slice s0 - 1 is the second
+// slice of lane - 1 (of lane + np - 1 for s0 = 0) and slice s0 + 2 the first
+// slice of lane + 1 (of lane - np + 1 for the last pair).
+struct PairLanes {
+  int up, dn;       // source lanes of slices s0 - 1 and s0 + 2
+  float fm, fp;     // their wrap factors (-m_f across the Ls boundary, else 1)
+};
+
 template <class S, int MU, bool FWD, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_dir2(float2 *acc, const char *in, long long soff, int cs,
-                                         int j, int s0, int Ls, const uint4 *lk, size_t ls,
-                                         const LsCoef &cf) {
+                                         int j, bool valid, int s0, int Ls, const uint4 *lk,
+                                         size_t ls, const LsCoef &cf, const PairLanes &pl) {
   float2 v[24];
   constexpr bool kFold = !PRE && !std::is_same<S, F32>::value;  // scales folded into the FMAs
   float2 sc = make_float2(1.f, 1.f);
   {
     float v0[24], v1[24];
-    if constexpr (kFold)
-      load24x2_unscaled<S>(in, soff, cs, j * Ls + s0, v0, v1, sc);
-    else
-      load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
+    if (valid) {
+      if constexpr (kFold)
+        load24x2_unscaled<S>(in, soff, cs, j * Ls + s0, v0, v1, sc);
+      else
+        load24x2<S>(in, soff, cs, j * Ls + s0, v0, v1);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 24; ++k) v0[k] = v1[k] = 0.f;
+    }
     if constexpr (PRE) {
       // M_phi on both slices as packed FMAs: (chi(s0), chi(s0+1)) =
-      // b (v(s0), v(s0+1)) + c (shifted neighbours)
+      // b (v(s0), v(s0+1)) + c (shifted neighbours); the outer halves come
+      // from the neighbouring lanes of the same site (all lanes take part)
       const float2 b2 = bc(cf.f.pre_b), c2 = bc(cf.f.pre_c);
-      const float mf = cf.f.mf;
-      float w[12];
-      const int sm = s0 == 0 ? Ls - 1 : s0 - 1;
-      const float fm = s0 == 0 ? -mf : 1.f;
-      load12<S, true>(in, soff, cs, j * Ls + sm, w);
 #pragma unroll
-      for (int k = 0; k < 12; ++k)  // upper: chi(s0) <- s0-1, chi(s0+1) <- s0
-        v[k] = __ffma2_rn(c2, make_float2(fm * w[k], v0[k]),
+      for (int k = 0; k < 12; ++k) {  // upper: chi(s0) <- s0-1, chi(s0+1) <- s0
+        const float w = __shfl_sync(0xffffffffu, v1[k], pl.up);
+        v[k] = __ffma2_rn(c2, make_float2(pl.fm * w, v0[k]),
                           __fmul2_rn(b2, make_float2(v0[k], v1[k])));
-      const int sp = s0 + 2 == Ls ? 0 : s0 + 2;
-      const float fp = s0 + 2 == Ls ? -mf : 1.f;
-      load12<S, false>(in, soff, cs, j * Ls + sp, w);
+      }
 #pragma unroll
-      for (int k = 0; k < 12; ++k)  // lower: chi(s0) <- s0+1, chi(s0+1) <- s0+2
-        v[12 + k] = __ffma2_rn(c2, make_float2(v1[12 + k], fp * w[k]),
+      for (int k = 0; k < 12; ++k) {  // lower: chi(s0) <- s0+1, chi(s0+1) <- s0+2
+        const float w = __shfl_sync(0xffffffffu, v0[12 + k], pl.dn);
+        v[12 + k] = __ffma2_rn(c2, make_float2(v1[12 + k], pl.fp * w),
                                __fmul2_rn(b2, make_float2(v0[12 + k], v1[12 + k])));
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < 24; ++k) v[k] = make_float2(v0[k], v1[k]);
     }
   }
-  float u[18];
-  load_link<S>(lk, ls, u, RC ? 1 : 0);
-  proj_mul_acc2<MU, FWD, DAG, kFold>(acc, v, u, sc);
+  if (valid) {
+    float u[18];
+    load_link<S>(lk, ls, u, RC ? 1 : 0);
+    proj_mul_acc2<MU, FWD, DAG, kFold>(acc, v, u, sc);
+  }
 }
 
 template <class S, int MU, bool DAG, bool PRE, bool RC>
 __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const char *in,
-                                        const uint4 *links, const int *nb, int site, int s0,
-                                        const LsCoef &cf) {
+                                        const uint4 *links, const int *nb, bool active, int site,
+                                        int s0, const LsCoef &cf, const PairLanes &pl) {
   constexpr int LC = RC ? S::kLinkChunksRecon : S::kLinkChunks;
-  const int jf = nb[2 * MU], jb = nb[2 * MU + 1];
+  const int jf = active ? nb[2 * MU] : -1, jb = active ? nb[2 * MU + 1] : -1;
   const size_t ls = (size_t)P.link_cs;
   const uint4 *lmu = links + (size_t)MU * LC * ls;
-  if (jf >= 0 && jf < P.in_limit)
-    hop_dir2<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, s0, P.Ls,
-                                    lmu + P.out_link_off + site, ls, cf);
-  if (jb >= 0 && jb < P.in_limit)
-    hop_dir2<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, s0, P.Ls,
-                                     lmu + P.in_link_off + jb, ls, cf);
+  const bool vf = jf >= 0 && jf < P.in_limit, vb = jb >= 0 && jb < P.in_limit;
+  if constexpr (PRE) {
+    // every lane takes part (the M_phi halves are exchanged between lanes)
+    hop_dir2<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, vf, s0, P.Ls,
+                                    lmu + P.out_link_off + site, ls, cf, pl);
+    hop_dir2<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, vb, s0, P.Ls,
+                                     lmu + P.in_link_off + jb, ls, cf, pl);
+  } else {
+    // no exchange between lanes: each lane branches on its own neighbours
+    if (vf)
+      hop_dir2<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, true, s0, P.Ls,
+                                      lmu + P.out_link_off + site, ls, cf, pl);
+    if (vb)
+      hop_dir2<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, true, s0, P.Ls,
+                                       lmu + P.in_link_off + jb, ls, cf, pl);
+  }
 }
 
 // The x-term of the Ls epilogue, out += (a0 + a1 S) x, on the thread's slices
@@ -524,19 +553,26 @@ __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const c
 // of its adjoint), (S x)_s = x_{s+1} with (S x)_{Ls-1} = -mf x_0 on the
 // others. Besides the pair it needs the down half of x at s0 - 1 and the up
 // half at s0 + 2.
+// Every lane of the warp calls this (the halves of slices s0 - 1 and s0 + 2
+// come from the neighbouring lanes); `have` is false where x is zero.
 template <class S, bool DAG>
 __device__ __forceinline__ void add_x_term2(float *o0, float *o1, const char *x, long long soff,
-                                            int cs, int site, int s0, int Ls,
-                                            const LsK<float> &c) {
+                                            int cs, int site, int s0, int Ls, bool have,
+                                            const LsK<float> &c, const PairLanes &pl) {
   float x0[12], x1[12], w[12];
   const int e = site * Ls + s0;
-  const float a0 = c.a0, a1 = c.a1, mf = c.mf;
-  const int sm = s0 == 0 ? Ls - 1 : s0 - 1;
-  const int sp = s0 + 2 == Ls ? 0 : s0 + 2;
-  const float fm = s0 == 0 ? -mf : 1.f, fp = s0 + 2 == Ls ? -mf : 1.f;
+  const float a0 = c.a0, a1 = c.a1;
+  const float fm = pl.fm, fp = pl.fp;
   // upper components: down for the operator, up for its adjoint
-  load12x2<S, true>(x, soff, cs, e, x0, x1);
-  load12<S, true>(x, soff, cs, site * Ls + (DAG ? sp : sm), w);
+  if (have) {
+    load12x2<S, true>(x, soff, cs, e, x0, x1);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x0[k] = x1[k] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k)
+    w[k] = DAG ? __shfl_sync(0xffffffffu, x0[k], pl.dn) : __shfl_sync(0xffffffffu, x1[k], pl.up);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     if (!DAG) {
@@ -548,8 +584,15 @@ __device__ __forceinline__ void add_x_term2(float *o0, float *o1, const char *x,
     }
   }
   // lower components: up for the operator, down for its adjoint
-  load12x2<S, false>(x, soff, cs, e, x0, x1);
-  load12<S, false>(x, soff, cs, site * Ls + (DAG ? sm : sp), w);
+  if (have) {
+    load12x2<S, false>(x, soff, cs, e, x0, x1);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x0[k] = x1[k] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k)
+    w[k] = DAG ? __shfl_sync(0xffffffffu, x1[k], pl.up) : __shfl_sync(0xffffffffu, x0[k], pl.dn);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     if (!DAG) {
@@ -566,20 +609,25 @@ __device__ __forceinline__ void add_x_term2(float *o0, float *o1, const char *x,
 // weigh on the plain hop's register allocation).
 template <class S, bool DAG, bool PRE, bool RC, bool EPI>
 __device__ __forceinline__ void hop2_body(const HopParams &P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const int rhs = blockIdx.z, blk = blockIdx.y;
   if (P.skip && P.skip[rhs]) return;
   if (P.bskip && P.bskip[rhs * P.nblocks + blk]) return;
   const int Ls = P.Ls, np = Ls >> 1;
-  const int nsites = P.nsites;  // blockDim.x is nsites * Ls / 2 rounded up to whole warps
-  const int tid = threadIdx.x;
-  const int jp = tid % np, sl = tid / np;
+  const int nsites = P.nsites;  // (blockDim.x / 32) * (32 / np): whole sites per warp
+  const int tid = threadIdx.x, lane = tid & 31, spw = 32 / np;
+  const int jp = lane % np, slw = lane / np;
+  const int sl = (tid >> 5) * spw + slw;
   const int s0 = 2 * jp;
   const int site0 = blockIdx.x * nsites;
   const int site = site0 + sl;
-  const bool active = (sl < nsites) && (site < P.n_out);
+  const bool active = (slw < spw) && (site < P.n_out);
   const LsCoef &cf = P.coef[rhs];
+  PairLanes pl;
+  pl.up = jp == 0 ? lane + np - 1 : lane - 1;
+  pl.dn = jp == np - 1 ? lane - (np - 1) : lane + 1;
+  pl.fm = jp == 0 ? -cf.f.mf : 1.f;
+  pl.fp = jp == np - 1 ? -cf.f.mf : 1.f;
 
   const char *in = P.in.data + blk * P.in.bstride + rhs * P.in.rstride;
   char *out = P.out.data + blk * P.out.bstride + rhs * P.out.rstride;
@@ -588,12 +636,14 @@ __device__ __forceinline__ void hop2_body(const HopParams &P) {
   float2 acc[24];
 #pragma unroll
   for (int k = 0; k < 24; ++k) acc[k] = make_float2(0.f, 0.f);
-  if (active) {
-    const int *nb = P.nbr + (size_t)site * 8;
-    hop_mu2<S, 0, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
-    hop_mu2<S, 1, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
-    hop_mu2<S, 2, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
-    hop_mu2<S, 3, DAG, PRE, RC>(acc, P, in, links, nb, site, s0, cf);
+  {
+    // every lane runs the direction loop (the M_phi halves are exchanged
+    // between lanes); inactive lanes load and add nothing
+    const int *nb = P.nbr + (size_t)(active ? site : 0) * 8;
+    hop_mu2<S, 0, DAG, PRE, RC>(acc, P, in, links, nb, active, site, s0, cf, pl);
+    hop_mu2<S, 1, DAG, PRE, RC>(acc, P, in, links, nb, active, site, s0, cf, pl);
+    hop_mu2<S, 2, DAG, PRE, RC>(acc, P, in, links, nb, active, site, s0, cf, pl);
+    hop_mu2<S, 3, DAG, PRE, RC>(acc, P, in, links, nb, active, site, s0, cf, pl);
   }
   const int e = site * Ls + s0;
   float a0[24], a1[24];
@@ -604,30 +654,75 @@ __device__ __forceinline__ void hop2_body(const HopParams &P) {
   }
 
   if constexpr (EPI) {
-    const int col = Ls + 1;
-    float *T = reinterpret_cast<float *>(smem_raw);
-    if (active) {
+    if (P.inv) {
+      // y = (1 - r S)^-1 v on the lanes of the site, as a scan (no shared
+      // memory). On the components where S takes s - 1: the wrap-free
+      // recursion yh_j = v_j + r yh_{j-1} (yh_0 = v_0) is a scan over the
+      // site's lanes with the constant factor r^2 per lane; the wrap then adds
+      // r^j d with d = -m_f r yh_{Ls-1} / (1 + m_f r^Ls) (the closed form's
+      // first element). Where S takes s + 1 the same runs in reversed order.
+      const LsK<float> &c = cf.f;
+      const float r = c.r, mfr = -c.mf * c.r * c.inv_den;
+      // r^(2 jp), r^(Ls - 2 - 2 jp) and r^(2 d) for the scan steps
+      float r_lo = 1.f, r_rev = 1.f;
+      for (int i = 0; i < 2 * jp; ++i) r_lo *= r;
+      for (int i = 0; i < Ls - 2 - 2 * jp; ++i) r_rev *= r;
+      const float r2 = r * r;
+      const int base = lane - jp;
 #pragma unroll
       for (int k = 0; k < 24; ++k) {
-        T[(sl * 24 + k) * col + s0] = a0[k];
-        T[(sl * 24 + k) * col + s0 + 1] = a1[k];
+        const bool down = (k < 12) != DAG;
+        // order the pair along the recursion: first, second
+        const float f = down ? a0[k] : a1[k], g = down ? a1[k] : a0[k];
+        const float w1 = g + r * f;
+        float C = w1;  // inclusive scan of w1 with factor r^2 per lane step
+        float m = r2;
+        for (int d = 1; d < np; d <<= 1) {
+          const float tu = __shfl_up_sync(0xffffffffu, C, d);
+          const float td = __shfl_down_sync(0xffffffffu, C, d);
+          if (down ? (jp >= d) : (jp + d < np)) C += m * (down ? tu : td);
+          m *= m;
+        }
+        const float cu = __shfl_up_sync(0xffffffffu, C, 1);
+        const float cd = __shfl_down_sync(0xffffffffu, C, 1);
+        const float cin = down ? (jp > 0 ? cu : 0.f) : (jp + 1 < np ? cd : 0.f);
+        const float last = __shfl_sync(0xffffffffu, C, down ? base + np - 1 : base);
+        const float dl = mfr * last;
+        // positions along the recursion: first at 2 jp (down) or Ls-2-2jp
+        // counted from the other end (up), second one further
+        const float rf = down ? r_lo : r_rev, rs = rf * r;
+        const float yf = f + r * cin + rf * dl;
+        const float ys = w1 + r2 * cin + rs * dl;
+        a0[k] = down ? yf : ys;
+        a1[k] = down ? ys : yf;
       }
     }
-    __syncthreads();
-    epilogue_columns<float>(T, nullptr, nsites, site0, P.n_out, Ls, DAG, P.inv, cf);
-    __syncthreads();
-    if (active) {
+    {
+      // q0 (p0 + p1 S) needs only the neighbouring slices: the pair's own and
+      // the outer ones from the neighbouring lanes of the site
+      const float p0 = cf.f.p0q, p1 = cf.f.p1q;
 #pragma unroll
       for (int k = 0; k < 24; ++k) {
-        a0[k] = T[(sl * 24 + k) * col + s0];
-        a1[k] = T[(sl * 24 + k) * col + s0 + 1];
+        const bool down = (k < 12) != DAG;  // S takes s - 1 on these components
+        const float wu = __shfl_sync(0xffffffffu, a1[k], pl.up);
+        const float wd = __shfl_sync(0xffffffffu, a0[k], pl.dn);
+        const float t0 = a0[k], t1 = a1[k];
+        if (down) {
+          a0[k] = p0 * t0 + p1 * (pl.fm * wu);
+          a1[k] = p0 * t1 + p1 * t0;
+        } else {
+          a0[k] = p0 * t0 + p1 * t1;
+          a1[k] = p0 * t1 + p1 * (pl.fp * wd);
+        }
       }
-      // the x-term after the column walk, in registers (no shared-memory copy
-      // of x, which would take L1 capacity from the gather)
-      if (P.has_x && site < P.xown_limit) {
-        const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
-        add_x_term2<S, DAG>(a0, a1, xo, P.xown.scale_off, P.xown.cs, site, s0, Ls, cf.f);
-      }
+    }
+    // the x-term after the column walk, in registers (no shared-memory copy
+    // of x, which would take L1 capacity from the gather); every lane takes
+    // part in the exchange of the outer halves
+    if (P.has_x) {
+      const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
+      add_x_term2<S, DAG>(a0, a1, xo, P.xown.scale_off, P.xown.cs, active ? site : 0, s0, Ls,
+                          active && site < P.xown_limit, cf.f, pl);
     }
   } else {
     const float q = cf.f.q0;
@@ -664,18 +759,18 @@ static bool hop_pairs(int Ls, dwf_prec p) { return p != DWF_FP64 && Ls % 2 == 0;
 int hop_sites_per_cta(int Ls, dwf_prec p) {
   int n;
   if (hop_pairs(Ls, p))
-    n = 128 / (Ls / 2);
+    n = 4 * (32 / (Ls / 2));  // four warps of whole sites
   else
     n = ((p == DWF_FP64) ? 128 : 256) / Ls;
   return n < 1 ? 1 : n;
 }
 
 size_t hop_smem_bytes(int Ls, dwf_prec p, int epi, int has_x) {
-  if (!epi) return 0;
+  // the two-slice kernel runs its Ls epilogue across the lanes of a site
+  if (!epi || hop_pairs(Ls, p)) return 0;
+  // the one-slice kernel walks the columns of T (and of x) in shared memory
   const size_t rs = (p == DWF_FP64) ? 8 : 4;
-  // the two-slice kernel adds x in registers; the one-slice kernel stages it
-  const int xbuf = (has_x && !hop_pairs(Ls, p)) ? 2 : 1;
-  return (size_t)hop_sites_per_cta(Ls, p) * 24 * (Ls + 1) * rs * xbuf;
+  return (size_t)hop_sites_per_cta(Ls, p) * 24 * (Ls + 1) * rs * (has_x ? 2 : 1);
 }
 
 template <class S, bool DAG, bool PRE, bool RC>
@@ -689,7 +784,7 @@ static void launch_t(const HopParams &P0, int nrhs, cudaStream_t st, dwf_prec pr
   if (grid.x == 0) return;
   if constexpr (!std::is_same<S, F64>::value) {
     if (hop_pairs(P.Ls, prec)) {
-      dim3 block((nsites * (P.Ls / 2) + 31) / 32 * 32);
+      dim3 block(128);
       if (P.epi) {
         hop2_kernel<S, DAG, PRE, RC, true><<<grid, block, smem, st>>>(P);
       } else {
@@ -737,8 +832,9 @@ void launch_hop(const HopParams &P, int dagger, int pre_mphi, int nrhs, cudaStre
     launch_t<S, false, false, false>(P, nrhs, st, p);
 }
 
-// Allow the hop kernels more than 48 KB of dynamic shared memory. Called once
-// per device before any launch (and so before any stream capture).
+// Allow the one-slice hop kernels more than 48 KB of dynamic shared memory
+// (the two-slice kernels use none). Called once per device before any launch
+// (and so before any stream capture).
 template <class K>
 static void allow_big_smem(K *kernel) {
   DWF_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -753,12 +849,6 @@ static void prepare_one() {
     allow_big_smem(hop_kernel<S, false, false, true>);
     allow_big_smem(hop_kernel<S, false, true, true>);
     allow_big_smem(hop_kernel<S, true, false, true>);
-    allow_big_smem(hop2_kernel<S, false, false, false, true>);
-    allow_big_smem(hop2_kernel<S, false, true, false, true>);
-    allow_big_smem(hop2_kernel<S, true, false, false, true>);
-    allow_big_smem(hop2_kernel<S, false, false, true, true>);
-    allow_big_smem(hop2_kernel<S, false, true, true, true>);
-    allow_big_smem(hop2_kernel<S, true, false, true, true>);
   }
 }
 void prepare_kernels() {
