@@ -22,6 +22,10 @@ solvers       CG, fixed-k inner CG, the Dirichlet block operator A_s with and
 pointwise     the hop at one (site, s), for spot checks on large lattices.
 slabs         A = D_PC^dag D_PC on large lattices, evaluated in time slabs
               by worker processes (A couples sites at most four apart).
+deflation     low modes of A by Chebyshev-filtered subspace iteration with
+              Rayleigh-Ritz, and MSPCG with the deflated start and the
+              additive coarse correction V Lambda^-1 V^dag (paper Sec. 1's
+              eigen-space methods combined with Algorithm 1).
 
 Parity status: every function is pinned by a CPU test against a closed form,
 an invariant, a dense brute-force computation or a library routine (see

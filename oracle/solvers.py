@@ -110,8 +110,9 @@ def cg_stop(apply_A, r, kmax: int, eps: float):
     return z, k
 
 
-def pcg(apply_A, apply_Minv, b, tol: float, maxiter: int = 100000):
-    """Algorithm 1: preconditioned CG on A x = b, x_0 = 0.
+def pcg(apply_A, apply_Minv, b, tol: float, maxiter: int = 100000, x0=None):
+    """Algorithm 1: preconditioned CG on A x = b, x_0 = 0 (or the given x0,
+    with r_0 = b - A x_0).
 
     alpha_k = <r_k, z_k> / <p_k, A p_k>; x += alpha p; r -= alpha A p;
     z = M^-1 r; beta_k = <z_{k+1}, r_{k+1}> / <z_k, r_k>; p = z + beta p.
@@ -119,8 +120,14 @@ def pcg(apply_A, apply_Minv, b, tol: float, maxiter: int = 100000):
     Returns (x, outer iterations, true relative residual).
     """
     bnorm = np.sqrt(op.norm2(b))
-    x = np.zeros_like(b)
-    r = b.copy()
+    if x0 is None:
+        x = np.zeros_like(b)
+        r = b.copy()
+    else:
+        x = x0.copy()
+        r = b - apply_A(x)
+        if np.sqrt(op.norm2(r)) <= tol * bnorm:
+            return x, 0, np.sqrt(op.norm2(r)) / bnorm
     z = apply_Minv(r)
     p = z.copy()
     rz = op.vdot(r, z).real
