@@ -1,5 +1,6 @@
 // Layout and precision conversions, gauge-link packing, and the standalone
 // Ls-direction operators M_5, M_5^-1 (paper Sec. 2.2 and eq. (dirac_equation)).
+#include <algorithm>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -58,7 +59,8 @@ void launch_ls_op(dwf_prec p, char *out, const char *in, long long rstride, int 
     P.coef[r] = coef[r];
     finalize_coef(P.coef[r]);
   }
-  const int nsites = hop_sites_per_cta(Ls, p);
+  // one thread per (site, s), at most 256 per CTA (128 for FP64)
+  const int nsites = std::max(1, (p == DWF_FP64 ? 128 : 256) / Ls);
   P.nsites = nsites;
   dim3 grid((nsite + nsites - 1) / nsites, 1, nrhs * coef_div), block((nsites * Ls + 31) / 32 * 32);
   // at most about 37 KB (nsites * Ls is at most 256): no opt-in beyond 48 KB

@@ -530,11 +530,14 @@ __device__ __forceinline__ void hop_mu2(float2 *acc, const HopParams &P, const c
   const uint4 *lmu = links + (size_t)MU * LC * ls;
   const bool vf = jf >= 0 && jf < P.in_limit, vb = jb >= 0 && jb < P.in_limit;
   if constexpr (PRE) {
-    // every lane takes part (the M_phi halves are exchanged between lanes)
-    hop_dir2<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, vf, s0, P.Ls,
-                                    lmu + P.out_link_off + site, ls, cf, pl);
-    hop_dir2<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, vb, s0, P.Ls,
-                                     lmu + P.in_link_off + jb, ls, cf, pl);
+    // every lane of the warp takes part (the M_phi halves are exchanged
+    // between lanes); a direction no lane of the warp has is skipped by all
+    if (__any_sync(0xffffffffu, vf))
+      hop_dir2<S, MU, true, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jf, vf, s0, P.Ls,
+                                      lmu + P.out_link_off + site, ls, cf, pl);
+    if (__any_sync(0xffffffffu, vb))
+      hop_dir2<S, MU, false, DAG, PRE, RC>(acc, in, P.in.scale_off, P.in.cs, jb, vb, s0, P.Ls,
+                                       lmu + P.in_link_off + jb, ls, cf, pl);
   } else {
     // no exchange between lanes: each lane branches on its own neighbours
     if (vf)
@@ -716,9 +719,8 @@ __device__ __forceinline__ void hop2_body(const HopParams &P) {
         }
       }
     }
-    // the x-term after the column walk, in registers (no shared-memory copy
-    // of x, which would take L1 capacity from the gather); every lane takes
-    // part in the exchange of the outer halves
+    // the x-term, (a0 + a1 S) x, after the Ls operator, in registers; every
+    // lane takes part in the exchange of the outer halves
     if (P.has_x) {
       const char *xo = P.xown.data + blk * P.xown.bstride + rhs * P.xown.rstride;
       add_x_term2<S, DAG>(a0, a1, xo, P.xown.scale_off, P.xown.cs, active ? site : 0, s0, Ls,
