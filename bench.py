@@ -355,8 +355,9 @@ class Timer:
             ts.append(e0.elapsed_time(e1) * 1e-3)
         return statistics.median(ts)
 
-    def solves(self, ctx, x, b, masses, prm, n, dist=None):
-        """n solves, each bracketed by (barrier +) synchronize and CUDA events."""
+    def solves(self, ctx, x, b, masses, prm, n, dist=None, defl=None):
+        """n solves, each bracketed by (barrier +) synchronize and CUDA events;
+        defl = (V, lambda, coarse): mspcg_solve_deflated."""
         import torch
         out = []
         for _ in range(n):
@@ -366,7 +367,10 @@ class Timer:
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(self.stream)
-            st, info = ctx.solve(x, b, masses, prm)
+            if defl is None:
+                st, info = ctx.solve(x, b, masses, prm)
+            else:
+                st, info = ctx.solve_deflated(x, b, masses, prm, *defl)
             e1.record(self.stream)
             torch.cuda.synchronize()
             if dist:
@@ -547,9 +551,73 @@ def run_gpu(args, rank, world, dist):
     return res, info_ms, info_plain
 
 
+def m5_timings(ctx, T, b, dims, Ls, nr):
+    """dwf_m5inv_gemm (tensor cores) on nr right-hand sides (the first nr
+    log-spaced masses of the 16-rhs workload) in FP32 and FP16, and the
+    CUDA-core closed form dwf_m5inv in FP32; b: one canonical source."""
+    from paper_1811_08488_gb300 import synthetic as syn
+    masses = list(syn.WORKLOADS[MULTI]["mf"])[:nr]
+    canon = b[:1].expand(nr, *b.shape[1:]).contiguous()
+    peak, _ = peaks()
+    m5 = {"nrhs": nr, "note": "call time: kernel + 4-byte status read + stream sync"}
+    Vh = int(np.prod(dims)) // 2
+    for prec, bpe in (("fp32", 96), ("fp16", 52)):
+        fi, fo = ctx.new_field(prec, nr), ctx.new_field(prec, nr)
+        ctx.field_import(fi, prec, canon, nr)
+        t = T.call(lambda: ctx.m5inv_gemm(fo, fi, 0, prec, masses), reps=10)
+        alg = 2 * Vh * Ls * bpe * nr
+        m5[prec] = {"us": round(t * 1e6, 1), "alg_bytes": alg, "gbs": round(alg / t / 1e9, 1),
+                    "frac": round(alg / t / 1e9 / peak, 4)}
+        if prec == "fp32":
+            t_cc = T.call(lambda: ctx.m5inv(fo, fi, 0, "fp32", masses), reps=10)
+            m5["closed_form_fp32"] = {"kernel": "ls_kernel (CUDA cores)", "us": round(t_cc * 1e6, 1),
+                                      "gbs": round(alg / t_cc / 1e9, 1)}
+        del fi, fo
+    return m5
+
+
+def deflation_timings(ctx, T, x, b, w, dist, n_ev=24):
+    """Low modes of A (dwf_eig_lowmodes: n_ev wanted, m = n_ev + 8, Chebyshev
+    degree 30, Ritz residuals <= 1e-5 lambda_max, seeded start vectors), then
+    plain CG and MSPCG deflated with them (start and coarse correction), three
+    timed solves each after an untimed two-iteration call."""
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    dims, Ls, mf = w["dims"], w["Ls"], float(w["mf"][0])
+    m = n_ev + 8
+    V = ctx.new_field("fp32", m)
+    rs = ctx.field_bytes("fp32", 1)
+    for b0 in range(0, m, 16):
+        k = min(16, m - b0)
+        start = torch.from_numpy(np.stack([syn.half_field(dims, Ls, 5000 + b0 + j)
+                                           for j in range(k)])).cuda()
+        ctx.field_import(V[b0 * rs:(b0 + k) * rs], "fp32", start, k)
+        del start
+    prm_e = dwf.default_eig_params(n_ev=n_ev, degree=30, max_passes=60, tol=1e-5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta, resid, einfo = ctx.eig_lowmodes(V, m, mf, prm_e)
+    t_eig = time.perf_counter() - t0
+    out = {"n_ev": n_ev, "m": m, "degree": 30,
+           "eig_seconds_wall": round(t_eig, 3), "eig_passes": einfo["passes"],
+           "eig_matvecs": einfo["matvecs"], "eig_converged": bool(einfo["converged"]),
+           "gap_theta_n_ev_over_theta_n_ev_minus_1": round(float(theta[n_ev] / theta[n_ev - 1]), 3)}
+    defl = (V[:n_ev * rs], theta[:n_ev], True)
+    for name, kw in (("plain_cg_deflated", dict(inner_iters=0)),
+                     ("mspcg_deflated", dict(inner_iters=INNER_K, block=w["block"]))):
+        T.solves(ctx, x, b, [mf], dwf.default_params(tol=1e-10, maxiter=2, **kw), 1, dist, defl)
+        r = T.solves(ctx, x, b, [mf], dwf.default_params(tol=1e-10, **kw), 3, dist, defl)
+        out[name] = {"seconds": round(statistics.mean(t for t, _, _ in r), 6),
+                     "outer_iters": r[-1][2][0]["outer_iters"],
+                     "converged": all(st == 0 and i[0]["converged"] for _, st, i in r)}
+    del V
+    return out
+
+
 def run_small(args, T, rank, dist):
     """The 16^3 x 32 x 12 workload: MSPCG (configured and autotuned blocks) and
-    plain CG, and the tensor-core M_5^-1 with 16 right-hand sides."""
+    plain CG, the tensor-core M_5^-1 with 16 right-hand sides, and the
+    deflated solves with 24 low modes."""
     import torch
     from paper_1811_08488_gb300 import dwf, synthetic as syn
     w = syn.WORKLOADS[SMALL]
@@ -578,26 +646,9 @@ def run_small(args, T, rank, dist):
                               "outer_iters": r[-1][2][0]["outer_iters"],
                               "converged": all(st == 0 and i[0]["converged"] for _, st, i in r)}
     # tensor-core M_5^-1, 16 right-hand sides of log-spaced masses (one call)
-    wm = syn.WORKLOADS[MULTI]
-    nr = len(wm["mf"])
-    canon16 = b.expand(nr, *b.shape[1:]).contiguous()
-    peak, _ = peaks()
-    m5 = {"nrhs": nr, "note": "call time: kernel + 4-byte status read + stream sync"}
-    Vh = int(np.prod(dims)) // 2
-    for prec, bpe in (("fp32", 96), ("fp16", 52)):
-        fi, fo = ctx.new_field(prec, nr), ctx.new_field(prec, nr)
-        ctx.field_import(fi, prec, canon16, nr)
-        t = T.call(lambda: ctx.m5inv_gemm(fo, fi, 0, prec, list(wm["mf"])), reps=10)
-        alg = 2 * Vh * Ls * bpe * nr
-        m5[prec] = {"us": round(t * 1e6, 1), "alg_bytes": alg, "gbs": round(alg / t / 1e9, 1),
-                    "frac": round(alg / t / 1e9 / peak, 4)}
-        if prec == "fp32":
-            t_cc = T.call(lambda: ctx.m5inv(fo, fi, 0, "fp32", list(wm["mf"])), reps=10)
-            m5["closed_form_fp32"] = {"kernel": "ls_kernel (CUDA cores)", "us": round(t_cc * 1e6, 1),
-                                      "gbs": round(alg / t_cc / 1e9, 1)}
-        del fi, fo
-    out["m5inv_gemm_16rhs"] = m5
-    del canon16, b, x
+    out["m5inv_gemm_16rhs"] = m5_timings(ctx, T, b, dims, Ls, len(syn.WORKLOADS[MULTI]["mf"]))
+    out["deflation"] = deflation_timings(ctx, T, x, b, w, dist)
+    del b, x
     ctx.close()
     torch.cuda.empty_cache()
     return out
@@ -690,6 +741,82 @@ def run_resident_study(args):
         del ctx
 
 
+def run_deflation_study(args):
+    """Low modes and deflated solves on one workload (one mass, `--nrhs`
+    seeded sources): the eigensolver's time, then plain CG and MSPCG (k = 6)
+    without deflation, with the deflated start only, and with the start plus
+    the coarse correction; every solve call takes all sources at once and is
+    timed with CUDA events after an untimed two-iteration call, L2 flushed."""
+    import torch
+    from paper_1811_08488_gb300 import dwf, synthetic as syn
+    name = args.workload
+    w = syn.WORKLOADS[name]
+    dims, Ls = w["dims"], w["Ls"]
+    mf = float(w["mf"][0])
+    U, _ = syn.workload_inputs(name)
+    ctx = dwf.Context(dims, Ls, b=w["b"], c=w["c"], M5=w["M5"])
+    ctx.gauge_load(U)
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    n_ev = args.n_ev
+    m = min(dwf.MAX_EIG, n_ev + max(8, n_ev // 4))
+    V = ctx.new_field("fp32", m)
+    rs = ctx.field_bytes("fp32", 1)
+    for b0 in range(0, m, 16):
+        k = min(16, m - b0)
+        start = torch.from_numpy(np.stack([syn.half_field(dims, Ls, 5000 + b0 + j)
+                                           for j in range(k)])).cuda()
+        ctx.field_import(V[b0 * rs:(b0 + k) * rs], "fp32", start, k)
+        del start
+    prm_e = dwf.default_eig_params(n_ev=n_ev, degree=args.degree, max_passes=60, tol=args.eig_tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta, resid, einfo = ctx.eig_lowmodes(V, m, mf, prm_e)
+    t_eig = time.perf_counter() - t0
+    print(json.dumps({"study": "deflate", "workload": name, "step": "eig_lowmodes", "m": m,
+                      "n_ev": n_ev, "degree": args.degree, "tol": args.eig_tol,
+                      "seconds": round(t_eig, 3), **einfo,
+                      "theta_over_lambda_max": [float(f"{t / einfo['lambda_max']:.4e}")
+                                                for t in theta[:n_ev + 1]],
+                      "max_resid_over_lambda_max": float(f"{resid[:n_ev].max() / einfo['lambda_max']:.3e}")}),
+          flush=True)
+    srcs = np.stack([syn.half_field(dims, Ls, 6000 + r) for r in range(args.nrhs)])
+    b = torch.from_numpy(srcs).cuda()
+    masses = [mf] * args.nrhs
+    Vd = V[:n_ev * rs]
+    lam = theta[:n_ev]
+
+    def timed(fn):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3, out
+
+    for k in (0, INNER_K):
+        base = dict(block=w["block"], inner="fp16", outer="fp32", inner_iters=k, tol=1e-10)
+        for mode in ("none", "start", "coarse"):
+            def call(maxiter=None):
+                prm = dwf.default_params(**dict(base, **({"maxiter": maxiter} if maxiter else {})))
+                x = torch.zeros_like(b)
+                if mode == "none":
+                    return ctx.solve(x, b, masses, prm, raise_on_error=False)
+                return ctx.solve_deflated(x, b, masses, prm, Vd, lam, coarse=mode == "coarse",
+                                          raise_on_error=False)
+            call(maxiter=2)
+            for _ in range(args.steps):
+                t, (st, info) = timed(call)
+                print(json.dumps({"study": "deflate", "workload": name, "solver":
+                                  "plain_cg" if k == 0 else f"mspcg_k{k}", "deflation": mode,
+                                  "n_ev": n_ev, "nrhs": args.nrhs, "seconds": round(t, 4),
+                                  "status": st, "outer_iters": [i["outer_iters"] for i in info],
+                                  "true_resid": [float(f"{i['true_resid']:.3e}") for i in info],
+                                  "converged": all(i["converged"] for i in info)}), flush=True)
+
+
 def run_study(args):
     """Time MSPCG / plain CG solves of one workload over a parameter sweep.
 
@@ -705,6 +832,8 @@ def run_study(args):
            to several times L2), timed warm and with L2 flushed
     delta  reliable-update threshold delta in {0.1, 0.03, 0.01, 0.001}, plain CG and k = 6
     flexible  Algorithm 1's Fletcher-Reeves beta vs the flexible Polak-Ribiere beta (k = 6)
+    deflate  low modes (dwf_eig_lowmodes) and deflated plain CG / MSPCG solves
+    m5     M_5^-1 on --nrhs right-hand sides: tensor cores (FP32, FP16) and CUDA cores
     Each configuration: one short untimed solve (plans, graphs), then
     `--steps` timed solves (CUDA events, L2 flushed before each). With
     `--maxiter` the solves stop after that many outer iterations and the
@@ -715,6 +844,19 @@ def run_study(args):
     torch.cuda.set_device(0)
     if args.study == "resident":
         run_resident_study(args)
+        return
+    if args.study == "deflate":
+        run_deflation_study(args)
+        return
+    if args.study == "m5":
+        # M_5^-1 on the 16^3x32 x Ls=12 lattice for --nrhs right-hand sides
+        w = syn.WORKLOADS[SMALL]
+        ctx = dwf.Context(w["dims"], w["Ls"], b=w["b"], c=w["c"], M5=w["M5"])
+        b = torch.from_numpy(syn.half_field(w["dims"], w["Ls"], 2002)[None].copy()).cuda()
+        flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        T = Timer(torch.cuda.current_stream(), flush)
+        print(json.dumps({"study": "m5", "workload": SMALL,
+                          **m5_timings(ctx, T, b, w["dims"], w["Ls"], args.nrhs)}), flush=True)
         return
     name = args.workload
     w = syn.WORKLOADS[name]
@@ -833,12 +975,16 @@ def main():
                     help="host-driven outer loop with eager launches (use_graph = 0), for "
                          "profilers that select kernels by launch")
     ap.add_argument("--study", choices=["k", "snake", "inner", "block", "rhs", "pair", "autotune", "delta",
-                                        "resident", "flexible"],
+                                        "resident", "flexible", "deflate", "m5"],
                     help="solver parameter sweep instead of the benchmark line")
     ap.add_argument("--workload", default=SMALL, help="workload of --study")
     ap.add_argument("--maxiter", type=int, default=0, help="outer-iteration cap of --study")
     ap.add_argument("--recon12", action="store_true", help="--study with reconstruct-12 links")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold of --study")
+    ap.add_argument("--n-ev", type=int, default=24, help="low modes of --study deflate")
+    ap.add_argument("--degree", type=int, default=30, help="Chebyshev degree of --study deflate")
+    ap.add_argument("--eig-tol", type=float, default=1e-5, help="Ritz residual tolerance of --study deflate")
+    ap.add_argument("--nrhs", type=int, default=4, help="sources of --study deflate / m5")
     args = ap.parse_args()
     if args.study:
         run_study(args)

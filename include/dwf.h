@@ -77,6 +77,7 @@ extern "C" {
 
 #define DWF_MAX_RHS 16
 #define DWF_MAX_LS 32
+#define DWF_MAX_EIG 64
 
 typedef enum {
   DWF_OK = 0,
@@ -137,6 +138,31 @@ typedef struct {
                        * its inner residual fell to inner_tol times its start  
                        * (at most inner_iters iterations)                     */
 } dwf_solver_params;
+
+/* Parameters of dwf_eig_lowmodes. Start from dwf_eig_params_default(). */
+typedef struct {
+  int n_ev;           /* wanted low modes, 1 .. m (the Ritz pairs tested for  
+                       * convergence; the other m - n_ev guard the subspace) */
+  int degree;         /* Chebyshev polynomial degree of one filter pass, >= 1 */
+  int max_passes;     /* filter passes at most, >= 0                          */
+  double tol;         /* stop once |A v - theta v| <= tol * lambda_max for the
+                       * n_ev lowest Ritz pairs; 0: run max_passes passes     */
+  double lambda_max;  /* upper bound of A's spectrum; <= 0: estimated as 1.1 x
+                       * the Rayleigh quotient after power_steps power
+                       * iterations from the first start vector              */
+  int power_steps;    /* power iterations of the estimate, >= 1               */
+  int schur;          /* the normal operator: 0 = D_PC^+ D_PC, 1 = D_sym^+ D_sym
+                       * (as dwf_solver_params.schur)                         */
+} dwf_eig_params;
+
+/* Result of dwf_eig_lowmodes. */
+typedef struct {
+  int passes;         /* filter passes done                                   */
+  int converged;      /* 1 when the n_ev lowest pairs met tol                 */
+  long long matvecs;  /* applications of A (one per vector)                   */
+  double lambda_max;  /* the upper bound used                                 */
+  double seconds;     /* wall time of the call                                */
+} dwf_eig_info;
 
 /* Per right-hand-side result of mspcg_solve. */
 typedef struct {
@@ -372,6 +398,61 @@ dwf_status dwf_autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const doubl
 dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs,
                        const double *mf, const dwf_solver_params *params,
                        dwf_solve_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Low modes and deflation (paper Sec. 1: for the many solves with one Dirac
+ * matrix of the measurement phase, low-lying eigenvectors computed once --
+ * EigCG, or Lanczos with a Chebyshev polynomial -- lower the effective
+ * condition number of every solve; here they are combined with MSPCG).
+ * ------------------------------------------------------------------------- */
+
+void dwf_eig_params_default(dwf_eig_params *p);
+
+/* Low modes of A = D_PC^+ D_PC (or D_sym^+ D_sym, p->schur) at quark mass mf by
+ * Chebyshev-filtered subspace iteration: a Rayleigh-Ritz step on the start
+ * vectors; then each pass replaces the subspace by T_d(L(A)) V, T_d the
+ * Chebyshev polynomial of degree p->degree and L mapping [theta_max,
+ * lambda_max] onto [-1, 1] (theta_max the largest current Ritz value), and
+ * takes the Ritz pairs of the filtered subspace (Gram matrices in FP64; the
+ * small generalised eigenproblem by Cholesky and Jacobi rotations on the
+ * device).
+ * V: m native FP32 fields (device, dwf_field_bytes(ctx, DWF_FP32, 1) bytes
+ *    apart), 1 <= m <= DWF_MAX_EIG, linearly independent start vectors on
+ *    entry (e.g. random); the orthonormal Ritz vectors in ascending order of
+ *    their Ritz values on return.
+ * theta, resid: host arrays of m: Ritz values and |A v - theta v|.
+ * info: host, may be NULL. Synchronous. The context allocates 2 m + 48
+ * FP32 half fields of work space on first use.
+ * Errors: INVALID_ARG, NO_GAUGE, NAN (the filtered subspace lost rank: fewer
+ * passes, a lower degree or other start vectors), CUDA. */
+dwf_status dwf_eig_lowmodes(dwf_ctx *ctx, void *V, int m, double mf, const dwf_eig_params *p,
+                            double *theta, double *resid, dwf_eig_info *info, void *stream);
+
+/* z = (accumulate ? z : 0) + V Lambda^-1 V^+ r for nrhs right-hand sides: the
+ * coarse correction of the deflated preconditioner (for exact eigenpairs
+ * V Lambda^-1 V^+ = A^-1 on span(V), 0 on its complement).
+ * V: n_ev native FP32 fields (dwf_field_bytes(ctx, DWF_FP32, 1) bytes apart),
+ * 1 <= n_ev <= DWF_MAX_EIG, orthonormal; lambda: host array of n_ev positive
+ * values; z, r: native fields of precision prec (DWF_FP32 or DWF_FP64) that
+ * do not alias.
+ * Errors: INVALID_ARG, CUDA. */
+dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, const double *lambda,
+                       int n_ev, dwf_prec prec, int nrhs, int accumulate, void *stream);
+
+/* mspcg_solve deflated with n_ev Ritz pairs (V, lambda as for dwf_deflate) of
+ * the solve's normal operator: the outer iteration starts from
+ * x_0 = V Lambda^-1 V^+ b (its residual recomputed in FP64), and with
+ * coarse = 1 the preconditioner becomes z = M^-1 r + V Lambda^-1 V^+ r (M the
+ * multisplitting preconditioner, or 1 for plain CG); with positive lambda the
+ * correction is Hermitian positive semi-definite, so Algorithm 1 is unchanged.
+ * V should hold eigenvectors of A at the right-hand sides' masses; others only
+ * weaken the deflation. Flexible PCG (params->flexible) is not supported with
+ * coarse = 1. Otherwise as mspcg_solve.
+ * Errors: as mspcg_solve, and UNSUPPORTED. */
+dwf_status mspcg_solve_deflated(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
+                                const dwf_solver_params *params, const void *V,
+                                const double *lambda, int n_ev, int coarse,
+                                dwf_solve_info *info, void *stream);
 
 /* Kernel timer for the Dslash (hop) kernels, the operator applications of
  * paper Sec. 2.2 that every solver step is made of (no counterpart in the

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdwf.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "autotune.cu", "blas.cu", "fields.cu", "geometry.cu", "hop.cu", "m5tc.cu", "noalloc.cu", "solver.cu"]
+SOURCES = ["api.cu", "autotune.cu", "blas.cu", "eig.cu", "fields.cu", "geometry.cu", "hop.cu", "m5tc.cu", "noalloc.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1,7 +1,9 @@
 // The C ABI (include/dwf.h): argument checks, context management, dispatch.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <vector>
 
 #include "solver.cuh"
 
@@ -123,6 +125,18 @@ void dwf_solver_params_default(dwf_solver_params *p) {
   p->flexible = 0;
   p->schur = 0;
   p->inner_tol = 0.0;
+}
+
+void dwf_eig_params_default(dwf_eig_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_ev = 16;
+  p->degree = 20;
+  p->max_passes = 30;
+  p->tol = 1e-6;
+  p->lambda_max = 0.0;
+  p->power_steps = 30;
+  p->schur = 0;
 }
 
 dwf_status dwf_gauge_load(dwf_ctx *ctx, const double *U, int on_device) {
@@ -441,8 +455,104 @@ dwf_status dwf_autotune_block(dwf_ctx *ctx, const void *b, int nrhs, const doubl
   API_CATCH(ctx)
 }
 
+static void check_lambda(const double *lambda, int n_ev) {
+  DWF_REQUIRE(n_ev >= 1 && n_ev <= DWF_MAX_EIG, DWF_ERR_INVALID_ARG, "n_ev must be in 1 .. 64");
+  DWF_REQUIRE(lambda != nullptr, DWF_ERR_INVALID_ARG, "null lambda");
+  for (int j = 0; j < n_ev; ++j)
+    DWF_REQUIRE(lambda[j] > 0 && std::isfinite(lambda[j]), DWF_ERR_INVALID_ARG,
+                "every lambda must be positive and finite");
+}
+
+dwf_status dwf_eig_lowmodes(dwf_ctx *ctx, void *V, int m, double mf, const dwf_eig_params *p,
+                            double *theta, double *resid, dwf_eig_info *info, void *stream) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && V && p && theta && resid, DWF_ERR_INVALID_ARG, "null argument");
+  DWF_REQUIRE(m >= 1 && m <= DWF_MAX_EIG, DWF_ERR_INVALID_ARG, "m must be in 1 .. 64");
+  DWF_REQUIRE(p->n_ev >= 1 && p->n_ev <= m, DWF_ERR_INVALID_ARG, "n_ev must be in 1 .. m");
+  DWF_REQUIRE(p->degree >= 1 && p->max_passes >= 0 && p->power_steps >= 1, DWF_ERR_INVALID_ARG,
+              "degree and power_steps must be >= 1, max_passes >= 0");
+  DWF_REQUIRE(p->tol >= 0 && std::isfinite(p->tol) && std::isfinite(p->lambda_max),
+              DWF_ERR_INVALID_ARG, "tol and lambda_max must be finite, tol >= 0");
+  DWF_REQUIRE(p->schur == 0 || p->schur == 1, DWF_ERR_INVALID_ARG, "schur must be 0 or 1");
+  DWF_REQUIRE(std::isfinite(mf), DWF_ERR_INVALID_ARG, "mass must be finite");
+  DWF_REQUIRE(ctx->have_gauge, DWF_ERR_NO_GAUGE, "no gauge field loaded");
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->own_stream;
+  if (!stream) DWF_CUDA_TRY(cudaDeviceSynchronize());
+  dwf::eig_lowmodes(ctx, (char *)V, m, mf, *p, theta, resid, info, st);
+  API_CATCH(ctx)
+}
+
+dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, const double *lambda,
+                       int n_ev, dwf_prec prec, int nrhs, int accumulate, void *stream) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && z && r && V, DWF_ERR_INVALID_ARG, "null argument");
+  DWF_REQUIRE(z != r, DWF_ERR_INVALID_ARG, "z and r must not alias");
+  DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_RHS, DWF_ERR_INVALID_ARG, "nrhs out of range");
+  DWF_REQUIRE(prec == DWF_FP32 || prec == DWF_FP64, DWF_ERR_INVALID_ARG,
+              "deflation fields must be FP32 or FP64");
+  check_lambda(lambda, n_ev);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cbytes = dwf::align_up(sizeof(double2) * DWF_MAX_EIG * DWF_MAX_RHS, 256);
+  const size_t lbytes = dwf::align_up(sizeof(double) * DWF_MAX_EIG, 256);
+  if (!ctx->defl.p) {
+    ctx->defl.ensure(cbytes + lbytes + dwf::dot_scratch_bytes());
+    DWF_CUDA_TRY(cudaMemset(ctx->defl.p, 0, ctx->defl.bytes));
+  }
+  std::vector<double> inv(n_ev);
+  for (int j = 0; j < n_ev; ++j) inv[j] = 1.0 / lambda[j];
+  double2 *c = ctx->defl.as<double2>();
+  double *inv_d = reinterpret_cast<double *>(ctx->defl.c() + cbytes);
+  DWF_CUDA_TRY(cudaMemcpyAsync(inv_d, inv.data(), sizeof(double) * n_ev, cudaMemcpyHostToDevice,
+                               st));
+  const int Vh = ctx->geo.Vh, Ls = ctx->act.Ls;
+  const long long cs = (long long)Vh * Ls;
+  dwf::VecSet Vs, Rs;
+  Vs.p = (const char *)V;
+  Vs.vs = (long long)dwf::field_rhs_bytes(DWF_FP32, Vh, Ls);
+  Vs.n = n_ev;
+  Rs.p = (const char *)r;
+  Rs.vs = (long long)dwf::field_rhs_bytes(prec, Vh, Ls);
+  Rs.n = nrhs;
+  Rs.prec = prec;
+  dwf::gram(Vs, Rs, cs, c, nrhs, dwf::dot_scratch_at(ctx->defl.c() + cbytes + lbytes), st);
+  dwf::combine(Vs, c, nrhs, inv_d, accumulate ? (const char *)z : nullptr, (char *)z, Rs.vs, prec,
+               nrhs, nullptr, cs, st);
+  // the host array must outlive its copy
+  DWF_CUDA_TRY(cudaStreamSynchronize(st));
+  API_CATCH(ctx)
+}
+
+static dwf_status solve_entry(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
+                              const dwf_solver_params *params, dwf_solve_info *info,
+                              void *stream, const dwf::DeflationInput *defl);
+
 dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
                        const dwf_solver_params *params, dwf_solve_info *info, void *stream) {
+  return solve_entry(ctx, x, b, nrhs, mf, params, info, stream, nullptr);
+}
+
+dwf_status mspcg_solve_deflated(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
+                                const dwf_solver_params *params, const void *V,
+                                const double *lambda, int n_ev, int coarse,
+                                dwf_solve_info *info, void *stream) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && V, DWF_ERR_INVALID_ARG, "null context or V");
+  check_lambda(lambda, n_ev);
+  DWF_REQUIRE(coarse == 0 || coarse == 1, DWF_ERR_INVALID_ARG, "coarse must be 0 or 1");
+  DWF_REQUIRE(!(coarse && params && params->flexible), DWF_ERR_UNSUPPORTED,
+              "flexible PCG with the coarse correction is not supported");
+  dwf::DeflationInput d;
+  d.V = (const char *)V;
+  d.lambda = lambda;
+  d.n_ev = n_ev;
+  d.coarse = coarse;
+  return solve_entry(ctx, x, b, nrhs, mf, params, info, stream, &d);
+  API_CATCH(ctx)
+}
+
+static dwf_status solve_entry(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
+                              const dwf_solver_params *params, dwf_solve_info *info,
+                              void *stream, const dwf::DeflationInput *defl) {
   API_TRY(ctx)
   check_common(ctx, nrhs, mf);
   check_params(params);
@@ -466,7 +576,7 @@ dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const dou
       for (int i = 0; i < 4; ++i) p.block[i] = it->second[i];
     }
   }
-  dwf_status s = dwf::solve(ctx, x, b, nrhs, mf, &p, info, st);
+  dwf_status s = dwf::solve(ctx, x, b, nrhs, mf, &p, info, st, defl);
   if (s != DWF_OK) {
     ctx->last_error = s == DWF_ERR_NOT_CONVERGED ? "not converged within maxiter"
                       : s == DWF_ERR_NAN         ? "NaN or Inf in a solver scalar"

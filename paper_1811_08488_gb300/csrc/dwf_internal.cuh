@@ -284,6 +284,10 @@ struct dwf_ctx {
   std::map<std::string, std::unique_ptr<dwf::BlockPlan>> block_plans;
   std::map<std::string, std::unique_ptr<dwf::SolverPlan>> solver_plans;
   std::map<std::string, std::array<int, 4>> tuned_blocks;  // autotuner results
+  // low modes (eig.cu): subspace W, A W, three batches of Chebyshev terms, and
+  // the small matrices and reduction scratch of the Rayleigh-Ritz step
+  dwf::DevBuf eig_w, eig_aw, eig_t, eig_small;
+  dwf::DevBuf defl;    // dwf_deflate: coefficients, 1/lambda, reduction scratch
   dwf::DevBuf prof;    // kProfSlots KernProf timer slots of the hop kernels
   int prof_on = 0;
   int unusable = 0;    // set after a device wait expired with work possibly in flight

@@ -633,7 +633,18 @@ struct SolveSetup {
   OuterArgs A;
   OpWork wlo, w64;
   DotSpec dot;
+  const Deflation *defl = nullptr;
 };
+
+// The coarse correction of the deflated preconditioner after z = M^-1 r (or
+// z = r + ... for plain CG, whose z is otherwise r itself).
+static void enqueue_coarse(SolveSetup &S, const int *skip, cudaStream_t st) {
+  if (!S.defl || !S.defl->coarse) return;
+  SolverPlan *sp = S.sp;
+  deflate_correct(*S.defl, sp->lo, sp->rlo.c(), sp->z.c(), S.A.rslo, S.nrhs,
+                  S.prm->inner_iters == 0 ? 1 : 0, sp->scal.as<OuterScalars>(), skip, S.A.cs,
+                  st);
+}
 
 static OpWork work_from(const DevBuf &d, dwf_prec p, const dwf_ctx *ctx, int nrhs) {
   const size_t rs = field_rhs_bytes(p, ctx->geo.Vh, ctx->act.Ls);
@@ -654,13 +665,14 @@ static void enqueue_iteration(SolveSetup &S, cudaStream_t st) {
   apply_mdagm(S.ctx, sp->Ap.p, sp->p.p, sp->lo, S.nrhs, S.mf, S.wlo, &S.dot, skip, st,
               S.prm->schur);
   outer_axpy_xr(sp->lo, A, S.nrhs, st);
-  if (!A.plain)
+  if (S.bp)
     block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
                        S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
                        (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo,
                        A.flexible ? sp->Ap.c() : nullptr,
                        A.flexible ? &sp->scal.as<OuterScalars>()->apz : nullptr,
                        S.prm->inner_tol, S.prm->schur);
+  enqueue_coarse(S, skip, st);
   outer_xpay_p(sp->lo, A, S.nrhs, st);
 }
 
@@ -676,10 +688,12 @@ static void enqueue_reliable_update(SolveSetup &S, cudaStream_t st) {
               S.prm->schur);
   outer_ru_residual(sp->lo, A, S.nrhs, st);
   if (!A.plain) {
-    block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
-                       S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo, nullptr,
-                       nullptr, S.prm->inner_tol, S.prm->schur);
+    if (S.bp)
+      block_precondition(S.ctx, S.bp, sp->z.c(), sp->rlo.c(), S.prm->inner_iters, S.prm->snake,
+                         S.nrhs, S.mf, &sp->scal.as<OuterScalars>()->rz_new,
+                         (int)(sizeof(OuterScalars) / sizeof(double)), skip, st, sp->lo,
+                         nullptr, nullptr, S.prm->inner_tol, S.prm->schur);
+    enqueue_coarse(S, skip, st);
     outer_set_rz(A, S.nrhs, st);
   }
 }
@@ -788,7 +802,8 @@ static void outer_hop_totals(dwf_ctx *ctx, dwf_prec p, cudaStream_t st, double &
 }
 
 dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
-                 const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st) {
+                 const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st,
+                 const DeflationInput *dfin) {
   const auto t0 = std::chrono::steady_clock::now();
   double hop_bytes0, hop_ns0;
   outer_hop_totals(ctx, prm->outer, st, hop_bytes0, hop_ns0);
@@ -797,12 +812,45 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
               "outer precision must be FP64 or FP32");
   DWF_REQUIRE(prm->tol > 0 && prm->maxiter > 0 && prm->inner_iters >= 0, DWF_ERR_INVALID_ARG,
               "tol, maxiter and inner_iters must be positive");
-  const bool plain = prm->inner_iters == 0;
+  const bool coarse = dfin && dfin->n_ev > 0 && dfin->coarse;
+  // plain CG keeps z = r unless the coarse correction makes z its own vector
+  const bool plain = prm->inner_iters == 0 && !coarse;
   SolverPlan *sp = get_solver_plan(ctx, lo, nrhs);
-  BlockPlan *bp = plain ? nullptr : get_block_plan(ctx, prm->block, prm->inner, nrhs, st);
+  BlockPlan *bp = prm->inner_iters == 0
+                      ? nullptr
+                      : get_block_plan(ctx, prm->block, prm->inner, nrhs, st);
   const int Vh = ctx->geo.Vh, Ls = ctx->act.Ls;
 
   SolveSetup S{ctx, sp, bp, prm, mf, nrhs};
+  Deflation defl;
+  if (dfin && dfin->n_ev > 0) {
+    DWF_REQUIRE(dfin->n_ev <= kMaxEig && dfin->V && dfin->lambda, DWF_ERR_INVALID_ARG,
+                "deflation: 1 .. 64 Ritz pairs with V and lambda");
+    const size_t cbytes = align_up(sizeof(double2) * kMaxEig * kMaxRhs, 256);
+    const size_t lbytes = align_up(sizeof(double) * kMaxEig, 256);
+    if (!sp->defl.p) {
+      sp->defl.ensure(cbytes + lbytes + dot_scratch_bytes());
+      DWF_CUDA_TRY(cudaMemsetAsync(sp->defl.p, 0, sp->defl.bytes, st));
+    }
+    std::vector<double> inv(dfin->n_ev);
+    for (int j = 0; j < dfin->n_ev; ++j) {
+      DWF_REQUIRE(dfin->lambda[j] > 0 && std::isfinite(dfin->lambda[j]), DWF_ERR_INVALID_ARG,
+                  "deflation: every lambda must be positive and finite");
+      inv[j] = 1.0 / dfin->lambda[j];
+    }
+    defl.V = dfin->V;
+    defl.vs = (long long)field_rhs_bytes(DWF_FP32, Vh, Ls);
+    defl.n_ev = dfin->n_ev;
+    defl.coarse = coarse ? 1 : 0;
+    defl.c = sp->defl.as<double2>();
+    defl.inv_lam = reinterpret_cast<const double *>(sp->defl.c() + cbytes);
+    defl.dw = dot_scratch_at(sp->defl.c() + cbytes + lbytes);
+    DWF_CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(defl.inv_lam), inv.data(),
+                                 sizeof(double) * dfin->n_ev, cudaMemcpyHostToDevice, st));
+    // the host vector must outlive the copy
+    DWF_CUDA_TRY(cudaStreamSynchronize(st));
+    S.defl = &defl;
+  }
   OuterArgs &A = S.A;
   A.b64 = sp->b64.c();
   A.r64 = sp->r64.c();
@@ -847,11 +895,20 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   DWF_CUDA_TRY(cudaMemsetAsync(sp->xlo.p, 0, sp->xlo.bytes, st));
   if (bp) DWF_CUDA_TRY(cudaMemsetAsync(bp->iters.p, 0, bp->iters.bytes, st));
   outer_init(lo, A, nrhs, st);
+  if (S.defl) {
+    // deflated start: x_0 = V Lambda^-1 V^+ b, r_0 = b - A x_0 in FP64
+    deflate_start(*S.defl, sp->b64.c(), sp->x64.c(), A.rs64, nrhs, A.cs, st);
+    apply_mdagm(ctx, sp->Ax64.p, sp->x64.p, DWF_FP64, nrhs, mf, S.w64, nullptr, nullptr, st,
+                prm->schur);
+    outer_ru_residual(lo, A, nrhs, st);
+  }
   if (!plain) {
-    block_precondition(ctx, bp, sp->z.c(), sp->rlo.c(), prm->inner_iters, prm->snake, nrhs, mf,
-                       &sp->scal.as<OuterScalars>()->rz_new,
-                       (int)(sizeof(OuterScalars) / sizeof(double)), nullptr, st, lo, nullptr,
-                       nullptr, prm->inner_tol, prm->schur);
+    if (bp)
+      block_precondition(ctx, bp, sp->z.c(), sp->rlo.c(), prm->inner_iters, prm->snake, nrhs,
+                         mf, &sp->scal.as<OuterScalars>()->rz_new,
+                         (int)(sizeof(OuterScalars) / sizeof(double)), nullptr, st, lo, nullptr,
+                         nullptr, prm->inner_tol, prm->schur);
+    enqueue_coarse(S, nullptr, st);
     outer_set_rz(A, nrhs, st);
   }
   outer_copy_p(lo, A, nrhs, st);
@@ -872,7 +929,9 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
   if (device_loop) {
     std::ostringstream key;
     key << (void *)bp << "/" << (bp ? bp->r.p : nullptr) << "/" << prm->inner_iters << "/"
-        << prm->snake << "/" << plain << "/" << A.flexible << "/" << ctx->prof_on;
+        << prm->snake << "/" << plain << "/" << A.flexible << "/" << ctx->prof_on << "/"
+        << (S.defl ? (const void *)S.defl->V : nullptr) << "/" << (S.defl ? S.defl->n_ev : 0)
+        << "/" << coarse;
     for (int r = 0; r < nrhs; ++r) key << "/" << mf[r];
     if (!sp->loop || sp->loop_key != key.str()) {
       sp->drop_graphs();

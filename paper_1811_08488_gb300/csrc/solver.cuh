@@ -3,6 +3,7 @@
 
 #include "blas.cuh"
 #include "dwf_internal.cuh"
+#include "eig.cuh"
 
 namespace dwf {
 
@@ -89,6 +90,7 @@ struct SolverPlan {
   DevBuf wlo, w64;  // operator temporaries
   DevBuf scal, partials, counters, opart, ocount, skip_iter, skip_ru;
   DevBuf ctl;  // SolveCtl of the device-driven loop
+  DevBuf defl;  // deflation: V^+ r coefficients, 1/lambda, reduction scratch
   OuterScalars *host_scal = nullptr;
   int *host_skip = nullptr;
   SolveCtl *host_ctl = nullptr;
@@ -98,8 +100,18 @@ struct SolverPlan {
   ~SolverPlan();
 };
 
+// defl (optional): deflation with Ritz pairs (V and n_ev; lambda on the host,
+// copied to the plan): the start x_0 = V Lambda^-1 V^+ b and, with coarse,
+// the coarse correction of the preconditioner.
+struct DeflationInput {
+  const char *V = nullptr;
+  const double *lambda = nullptr;  // host [n_ev]
+  int n_ev = 0;
+  int coarse = 0;
+};
 dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
-                 const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st);
+                 const dwf_solver_params *prm, dwf_solve_info *info, cudaStream_t st,
+                 const DeflationInput *defl = nullptr);
 
 // Block-shape autotuner (csrc/autotune.cu).
 std::vector<std::array<int, 4>> block_candidates(const int dims[4]);

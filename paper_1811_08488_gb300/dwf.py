@@ -23,6 +23,7 @@ PREC = {"fp64": DWF_FP64, "fp32": DWF_FP32, "fp16": DWF_FP16, "bf16": DWF_BF16}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NOT_CONVERGED",
           5: "TIMEOUT", 6: "NAN", 7: "NO_GAUGE"}
 MAX_RHS = 16
+MAX_EIG = 64
 NOALLOC_SCRATCH_BYTES = 24 << 20
 
 # Every symbol include/dwf.h declares.
@@ -32,7 +33,8 @@ EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_def
            "dwf_block_apply",
            "dwf_block_precond", "dwf_autotune_block", "dwf_source_prep", "dwf_odd_reconstruct",
            "dwf_mpc_sym", "dwf_mdagm_sym", "dwf_source_prep_sym",
-           "mspcg_solve", "dwf_profile_enable", "dwf_profile_read"]
+           "mspcg_solve", "dwf_profile_enable", "dwf_profile_read",
+           "dwf_eig_params_default", "dwf_eig_lowmodes", "dwf_deflate", "mspcg_solve_deflated"]
 
 
 class DwfError(RuntimeError):
@@ -52,6 +54,20 @@ class SolverParams(C.Structure):
                 ("delta", C.c_double), ("snake", C.c_int), ("use_graph", C.c_int),
                 ("io_on_host", C.c_int), ("check_every", C.c_int), ("flexible", C.c_int),
                 ("schur", C.c_int), ("inner_tol", C.c_double)]
+
+
+class EigParams(C.Structure):
+    _fields_ = [("n_ev", C.c_int), ("degree", C.c_int), ("max_passes", C.c_int),
+                ("tol", C.c_double), ("lambda_max", C.c_double), ("power_steps", C.c_int),
+                ("schur", C.c_int)]
+
+
+class EigInfo(C.Structure):
+    _fields_ = [("passes", C.c_int), ("converged", C.c_int), ("matvecs", C.c_longlong),
+                ("lambda_max", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SolveInfo(C.Structure):
@@ -104,6 +120,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_block_precond": (I, [P, P, P, C.POINTER(SolverParams), I, D, P]),
         "mspcg_solve": (I, [P, P, P, I, D, C.POINTER(SolverParams), C.POINTER(SolveInfo), P]),
         "dwf_profile_enable": (I, [P, I]),
+        "dwf_eig_params_default": (None, [C.POINTER(EigParams)]),
+        "dwf_eig_lowmodes": (I, [P, P, I, C.c_double, C.POINTER(EigParams), D, D,
+                                 C.POINTER(EigInfo), P]),
+        "dwf_deflate": (I, [P, P, P, P, D, I, I, I, I, P]),
+        "mspcg_solve_deflated": (I, [P, P, P, I, D, C.POINTER(SolverParams), P, D, I, I,
+                                     C.POINTER(SolveInfo), P]),
         "dwf_profile_read": (I, [P, C.POINTER(KernelTime), I, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -134,6 +156,14 @@ def default_params(**kw) -> SolverParams:
             setattr(p, k, PREC[v])
         else:
             setattr(p, k, v)
+    return p
+
+
+def default_eig_params(**kw) -> EigParams:
+    p = EigParams()
+    lib().dwf_eig_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
     return p
 
 
@@ -370,6 +400,46 @@ class Context:
         bp = b.ctypes.data if isinstance(b, np.ndarray) else _ptr(b)
         st = lib().mspcg_solve(self._h, C.c_void_p(xp), C.c_void_p(bp), m.size, mp,
                                C.byref(params), infos, _stream(stream))
+        if st != 0 and raise_on_error and st != 4:
+            raise DwfError(st, lib().dwf_last_error(self._h).decode())
+        return st, [i.as_dict() for i in infos]
+
+    # ------------------------------------------------------ low modes, deflation
+    def eig_lowmodes(self, V, m, mf, params, stream=None):
+        """dwf_eig_lowmodes: V holds m native FP32 fields (start vectors in,
+        Ritz vectors out, ascending). Returns (theta, resid, info dict)."""
+        theta = np.zeros(m)
+        resid = np.zeros(m)
+        info = EigInfo()
+        self._check(lib().dwf_eig_lowmodes(self._h, C.c_void_p(_ptr(V)), int(m), float(mf),
+                                           C.byref(params),
+                                           theta.ctypes.data_as(C.POINTER(C.c_double)),
+                                           resid.ctypes.data_as(C.POINTER(C.c_double)),
+                                           C.byref(info), _stream(stream)))
+        return theta, resid, info.as_dict()
+
+    def deflate(self, z, r, V, lam, prec, nrhs=1, accumulate=False, stream=None):
+        """dwf_deflate: z = (z if accumulate) + V Lambda^-1 V^+ r."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self._check(lib().dwf_deflate(self._h, C.c_void_p(_ptr(z)), C.c_void_p(_ptr(r)),
+                                      C.c_void_p(_ptr(V)),
+                                      lam.ctypes.data_as(C.POINTER(C.c_double)), lam.size,
+                                      PREC.get(prec, prec), int(nrhs), int(bool(accumulate)),
+                                      _stream(stream)))
+
+    def solve_deflated(self, x, b, mf, params, V, lam, coarse=True, stream=None,
+                       raise_on_error=True):
+        """mspcg_solve_deflated with the Ritz pairs (V, lam). Returns (status,
+        [info dict per rhs])."""
+        m, mp = _masses(mf)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        infos = (SolveInfo * m.size)()
+        xp = x.ctypes.data if isinstance(x, np.ndarray) else _ptr(x)
+        bp = b.ctypes.data if isinstance(b, np.ndarray) else _ptr(b)
+        st = lib().mspcg_solve_deflated(self._h, C.c_void_p(xp), C.c_void_p(bp), m.size, mp,
+                                        C.byref(params), C.c_void_p(_ptr(V)),
+                                        lam.ctypes.data_as(C.POINTER(C.c_double)), lam.size,
+                                        int(bool(coarse)), infos, _stream(stream))
         if st != 0 and raise_on_error and st != 4:
             raise DwfError(st, lib().dwf_last_error(self._h).decode())
         return st, [i.as_dict() for i in infos]

@@ -52,6 +52,9 @@ def test_binding_struct_layouts_match_header(libpath):
     assert p.outer == dwf.DWF_FP32 and p.inner == dwf.DWF_FP16
     assert p.delta == 0.001 and p.snake == 1 and p.use_graph == 1 and p.check_every == 10
     assert p.flexible == 0
+    e = dwf.default_eig_params()
+    assert e.n_ev == 16 and e.degree == 20 and e.max_passes == 30 and e.tol == 1e-6
+    assert e.lambda_max == 0.0 and e.power_steps == 30 and e.schur == 0
 
 
 def c_layout(struct, fields, tmp_path):
@@ -73,7 +76,9 @@ def c_layout(struct, fields, tmp_path):
 @pytest.mark.parametrize("cname,pyname", [("dwf_action", "Action"),
                                           ("dwf_solver_params", "SolverParams"),
                                           ("dwf_solve_info", "SolveInfo"),
-                                          ("dwf_kernel_time", "KernelTime")])
+                                          ("dwf_kernel_time", "KernelTime"),
+                                          ("dwf_eig_params", "EigParams"),
+                                          ("dwf_eig_info", "EigInfo")])
 def test_binding_structs_match_the_c_layout(cname, pyname, tmp_path):
     """Every ctypes struct of the binding has the size and field offsets that a
     C compiler gives the header's struct (dwf_solve_info includes dslash_gbs)."""
