@@ -798,6 +798,8 @@ def run_deflation_study(args):
 
     for k in (0, INNER_K):
         base = dict(block=w["block"], inner="fp16", outer="fp32", inner_iters=k, tol=1e-10)
+        if args.eager:
+            base["use_graph"] = 0
         for mode in ("none", "start", "coarse"):
             def call(maxiter=None):
                 prm = dwf.default_params(**dict(base, **({"maxiter": maxiter} if maxiter else {})))

@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(kEigThreads) gram_skinny_kernel(const GramArgs
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tile = blockIdx.y, ibase = tile * 8 * NI;
   KahanF acc[NI][NJ][2];
+  // unrolled so that two elements' loads are in flight per warp
+#pragma unroll 2
   for (long long i = blockIdx.x * 32LL + lane; i < a.n4; i += gridDim.x * 32LL) {
     float y[NJ][4];
 #pragma unroll
