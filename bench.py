@@ -59,7 +59,12 @@ MSPCG_OUTER_ITERS_RECORDED = 193
 # of the timed MSPCG solves, from one ncu capture of the headline workload;
 # valid only while the hop kernel sources hash to `source_sha` (otherwise the
 # line reports traffic null).
-KNOWN_TRAFFIC = {}
+KNOWN_TRAFFIC = {
+    # one-pass ncu capture of 4 launches inside the timed solve of the bench
+    # command (profiles/hop_fp16_block_adjoint_mobius_24x24x24x64_Ls16.md):
+    # dram__bytes_read.sum + dram__bytes_write.sum, mean per launch
+    "hop2_kernel<F16,1,0,0,1> [block]": {"bytes": 1799313536, "source_sha": "a5428b9e50878f1d"},
+}
 HOP_SOURCES = ["paper_1811_08488_gb300/csrc/hop.cu", "paper_1811_08488_gb300/csrc/device_common.cuh",
                "paper_1811_08488_gb300/csrc/dwf_internal.cuh"]
 
