@@ -53,7 +53,7 @@ INNER_K = 6
 # solve the workload (hours of CPU time), so it scales its sample by this
 # count and says so; the GB300 arm's own cpu_baseline uses the count it
 # measured in the same run.
-MSPCG_OUTER_ITERS_RECORDED = 193
+MSPCG_OUTER_ITERS_RECORDED = 192
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
 # of the timed MSPCG solves, from one ncu capture of the headline workload;
@@ -789,6 +789,9 @@ def run_deflation_study(args):
     b = torch.from_numpy(srcs).cuda()
     masses = [mf] * args.nrhs
     Vd = V[:n_ev * rs]
+    if args.vprec != "fp32":
+        Vd = ctx.new_field(args.vprec, n_ev)
+        ctx.field_convert(Vd, args.vprec, V, "fp32", n_ev)
     lam = theta[:n_ev]
 
     def timed(fn):
@@ -812,12 +815,13 @@ def run_deflation_study(args):
                 if mode == "none":
                     return ctx.solve(x, b, masses, prm, raise_on_error=False)
                 return ctx.solve_deflated(x, b, masses, prm, Vd, lam, coarse=mode == "coarse",
-                                          raise_on_error=False)
+                                          vprec=args.vprec, raise_on_error=False)
             call(maxiter=2)
             for _ in range(args.steps):
                 t, (st, info) = timed(call)
                 print(json.dumps({"study": "deflate", "workload": name, "solver":
                                   "plain_cg" if k == 0 else f"mspcg_k{k}", "deflation": mode,
+                                  "vprec": args.vprec,
                                   "n_ev": n_ev, "nrhs": args.nrhs, "seconds": round(t, 4),
                                   "status": st, "outer_iters": [i["outer_iters"] for i in info],
                                   "true_resid": [float(f"{i['true_resid']:.3e}") for i in info],
@@ -837,7 +841,7 @@ def run_study(args):
     resident  the k = 6 block preconditioner alone, per 8^3 x 16 block, on
            lattices of 2 to 32 such blocks (working set from well inside L2
            to several times L2), timed warm and with L2 flushed
-    delta  reliable-update threshold delta in {0.1, 0.03, 0.01, 0.001}, plain CG and k = 6
+    delta  reliable-update threshold delta in {0.1, 0.03, 0.01, 0.001, 0.0001}, plain CG and k = 6
     flexible  Algorithm 1's Fletcher-Reeves beta vs the flexible Polak-Ribiere beta (k = 6)
     deflate  low modes (dwf_eig_lowmodes) and deflated plain CG / MSPCG solves
     m5     M_5^-1 on --nrhs right-hand sides: tensor cores (FP32, FP16) and CUDA cores
@@ -899,7 +903,8 @@ def run_study(args):
     elif args.study == "flexible":
         configs = [dict(base, flexible=f) for f in (0, 1)]
     elif args.study == "delta":
-        configs = [dict(base, inner_iters=k, delta=d) for k in (0, 6) for d in (0.1, 0.03, 0.01, 0.001)]
+        configs = [dict(base, inner_iters=k, delta=d) for k in (0, 6)
+                   for d in (0.1, 0.03, 0.01, 0.001, 0.0001)]
     elif args.study == "autotune":
         # the autotuner's pick (20 trial outer iterations per candidate), then
         # the full solve with block = 0 (the remembered pick)
@@ -992,6 +997,8 @@ def main():
     ap.add_argument("--degree", type=int, default=30, help="Chebyshev degree of --study deflate")
     ap.add_argument("--eig-tol", type=float, default=1e-5, help="Ritz residual tolerance of --study deflate")
     ap.add_argument("--nrhs", type=int, default=4, help="sources of --study deflate / m5")
+    ap.add_argument("--vprec", default="fp32", choices=["fp32", "fp16"],
+                    help="storage of the low modes in the deflated solves of --study deflate")
     args = ap.parse_args()
     if args.study:
         run_study(args)

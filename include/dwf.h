@@ -238,6 +238,13 @@ dwf_status dwf_field_export(dwf_ctx *ctx, void *canon_out, int canon_is_fp32,
                             const void *native_in, dwf_prec prec, int nrhs,
                             void *stream);
 
+/* Native -> native conversion of nrhs (1 .. DWF_MAX_EIG) half fields from
+ * precision in_prec to out_prec (e.g. FP32 low modes to FP16 for
+ * mspcg_solve_deflated); FP16/BF16 outputs compute the per-(site, s) scale.
+ * The fields must not overlap. Errors: INVALID_ARG, CUDA. */
+dwf_status dwf_field_convert(dwf_ctx *ctx, void *native_out, dwf_prec out_prec,
+                             const void *native_in, dwf_prec in_prec, int nrhs, void *stream);
+
 /* Hopping block M^4 (paper Sec. 2.2, M^4_{eo/oe} = D^w M_phi):
  *   dagger = 0:  out = -1/2 Dhop (M_phi in)            (M^4_eo or M^4_oe)
  *   dagger = 1:  out = -1/2 M_phi^+ Dhop^+ in          ((M^4)^+)
@@ -431,15 +438,18 @@ dwf_status dwf_eig_lowmodes(dwf_ctx *ctx, void *V, int m, double mf, const dwf_e
 /* z = (accumulate ? z : 0) + V Lambda^-1 V^+ r for nrhs right-hand sides: the
  * coarse correction of the deflated preconditioner (for exact eigenpairs
  * V Lambda^-1 V^+ = A^-1 on span(V), 0 on its complement).
- * V: n_ev native FP32 fields (dwf_field_bytes(ctx, DWF_FP32, 1) bytes apart),
- * 1 <= n_ev <= DWF_MAX_EIG, orthonormal; lambda: host array of n_ev positive
- * values; z, r: native fields of precision prec (DWF_FP32 or DWF_FP64) that
- * do not alias.
- * Errors: INVALID_ARG, CUDA. */
-dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, const double *lambda,
-                       int n_ev, dwf_prec prec, int nrhs, int accumulate, void *stream);
+ * V: n_ev native fields of precision vprec (DWF_FP32, or DWF_FP16 with its
+ * per-(site, s) scales, which halves the bytes read; dwf_field_bytes(ctx,
+ * vprec, 1) bytes apart), 1 <= n_ev <= DWF_MAX_EIG, orthonormal; lambda: host
+ * array of n_ev positive values; z, r: native fields of precision prec
+ * (DWF_FP32 or DWF_FP64) that do not alias. FP16 V serves at most 4
+ * right-hand sides per call.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, dwf_prec vprec,
+                       const double *lambda, int n_ev, dwf_prec prec, int nrhs, int accumulate,
+                       void *stream);
 
-/* mspcg_solve deflated with n_ev Ritz pairs (V, lambda as for dwf_deflate) of
+/* mspcg_solve deflated with n_ev Ritz pairs (V, vprec, lambda as for dwf_deflate) of
  * the solve's normal operator: the outer iteration starts from
  * x_0 = V Lambda^-1 V^+ b (its residual recomputed in FP64), and with
  * coarse = 1 the preconditioner becomes z = M^-1 r + V Lambda^-1 V^+ r (M the
@@ -450,7 +460,7 @@ dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, cons
  * coarse = 1. Otherwise as mspcg_solve.
  * Errors: as mspcg_solve, and UNSUPPORTED. */
 dwf_status mspcg_solve_deflated(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
-                                const dwf_solver_params *params, const void *V,
+                                const dwf_solver_params *params, const void *V, dwf_prec vprec,
                                 const double *lambda, int n_ev, int coarse,
                                 dwf_solve_info *info, void *stream);
 

@@ -194,6 +194,21 @@ dwf_status dwf_field_export(dwf_ctx *ctx, void *canon_out, int canon_is_fp32,
   API_CATCH(ctx)
 }
 
+dwf_status dwf_field_convert(dwf_ctx *ctx, void *native_out, dwf_prec out_prec,
+                             const void *native_in, dwf_prec in_prec, int nrhs, void *stream) {
+  API_TRY(ctx)
+  DWF_REQUIRE(ctx && native_out && native_in, DWF_ERR_INVALID_ARG, "null argument");
+  DWF_REQUIRE(native_out != native_in, DWF_ERR_INVALID_ARG, "aliased fields");
+  DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_EIG, DWF_ERR_INVALID_ARG, "nrhs out of range");
+  DWF_REQUIRE(out_prec >= DWF_FP64 && out_prec <= DWF_BF16 && in_prec >= DWF_FP64 &&
+                  in_prec <= DWF_BF16,
+              DWF_ERR_INVALID_ARG, "unknown precision");
+  DWF_CUDA_TRY(cudaSetDevice(ctx->device));
+  dwf::launch_convert(out_prec, (char *)native_out, in_prec, (const char *)native_in,
+                      ctx->geo.Vh, ctx->act.Ls, nrhs, (cudaStream_t)stream);
+  API_CATCH(ctx)
+}
+
 dwf_status dwf_dslash_eo(dwf_ctx *ctx, void *out, const void *in, int out_parity, int dagger,
                          dwf_prec prec, int nrhs, const double *mf, void *stream) {
   API_TRY(ctx)
@@ -482,14 +497,19 @@ dwf_status dwf_eig_lowmodes(dwf_ctx *ctx, void *V, int m, double mf, const dwf_e
   API_CATCH(ctx)
 }
 
-dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, const double *lambda,
-                       int n_ev, dwf_prec prec, int nrhs, int accumulate, void *stream) {
+dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, dwf_prec vprec,
+                       const double *lambda, int n_ev, dwf_prec prec, int nrhs, int accumulate,
+                       void *stream) {
   API_TRY(ctx)
   DWF_REQUIRE(ctx && z && r && V, DWF_ERR_INVALID_ARG, "null argument");
   DWF_REQUIRE(z != r, DWF_ERR_INVALID_ARG, "z and r must not alias");
   DWF_REQUIRE(nrhs >= 1 && nrhs <= DWF_MAX_RHS, DWF_ERR_INVALID_ARG, "nrhs out of range");
   DWF_REQUIRE(prec == DWF_FP32 || prec == DWF_FP64, DWF_ERR_INVALID_ARG,
               "deflation fields must be FP32 or FP64");
+  DWF_REQUIRE(vprec == DWF_FP32 || vprec == DWF_FP16, DWF_ERR_INVALID_ARG,
+              "V must be FP32 or FP16");
+  DWF_REQUIRE(nrhs <= 4 || vprec == DWF_FP32, DWF_ERR_UNSUPPORTED,
+              "FP16 V serves at most 4 right-hand sides per call");
   check_lambda(lambda, n_ev);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t cbytes = dwf::align_up(sizeof(double2) * DWF_MAX_EIG * DWF_MAX_RHS, 256);
@@ -508,8 +528,10 @@ dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, cons
   const long long cs = (long long)Vh * Ls;
   dwf::VecSet Vs, Rs;
   Vs.p = (const char *)V;
-  Vs.vs = (long long)dwf::field_rhs_bytes(DWF_FP32, Vh, Ls);
+  Vs.vs = (long long)dwf::field_rhs_bytes(vprec, Vh, Ls);
   Vs.n = n_ev;
+  Vs.prec = vprec;
+  Vs.soff = (long long)dwf::align_up(dwf::field_data_bytes(vprec, Vh, Ls), 256);
   Rs.p = (const char *)r;
   Rs.vs = (long long)dwf::field_rhs_bytes(prec, Vh, Ls);
   Rs.n = nrhs;
@@ -532,17 +554,22 @@ dwf_status mspcg_solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const dou
 }
 
 dwf_status mspcg_solve_deflated(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *mf,
-                                const dwf_solver_params *params, const void *V,
+                                const dwf_solver_params *params, const void *V, dwf_prec vprec,
                                 const double *lambda, int n_ev, int coarse,
                                 dwf_solve_info *info, void *stream) {
   API_TRY(ctx)
   DWF_REQUIRE(ctx && V, DWF_ERR_INVALID_ARG, "null context or V");
   check_lambda(lambda, n_ev);
   DWF_REQUIRE(coarse == 0 || coarse == 1, DWF_ERR_INVALID_ARG, "coarse must be 0 or 1");
+  DWF_REQUIRE(vprec == DWF_FP32 || vprec == DWF_FP16, DWF_ERR_INVALID_ARG,
+              "V must be FP32 or FP16");
+  DWF_REQUIRE(nrhs <= 4 || vprec == DWF_FP32, DWF_ERR_UNSUPPORTED,
+              "FP16 V serves at most 4 right-hand sides per call");
   DWF_REQUIRE(!(coarse && params && params->flexible), DWF_ERR_UNSUPPORTED,
               "flexible PCG with the coarse correction is not supported");
   dwf::DeflationInput d;
   d.V = (const char *)V;
+  d.vprec = vprec;
   d.lambda = lambda;
   d.n_ev = n_ev;
   d.coarse = coarse;

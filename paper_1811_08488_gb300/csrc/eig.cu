@@ -16,6 +16,7 @@
 // FP64. The vector kernels are HBM-bound; the dense kernel works on at most
 // 64 x 64 matrices.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <type_traits>
@@ -48,12 +49,70 @@ DotScratch dot_scratch_at(char *base) {
   return w;
 }
 
+// CTAs of one full wave of kernel K (kEigThreads threads, no dynamic shared
+// memory) on the current device: the grid-stride vector kernels are launched
+// with one wave, split over their tiles, so that no partial second wave
+// trails them.
+template <auto K>
+static int wave_ctas() {
+  constexpr int kDevices = 64;
+  static std::atomic<int> cache[kDevices];  // per device; 0 until computed
+  int dev = 0;
+  DWF_CUDA_TRY(cudaGetDevice(&dev));
+  std::atomic<int> *slot = dev < kDevices ? &cache[dev] : nullptr;
+  if (slot) {
+    const int n = slot->load(std::memory_order_relaxed);
+    if (n > 0) return n;
+  }
+  int nsm = 0, per = 0;
+  DWF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  DWF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, kEigThreads, 0));
+  const int n = std::max(1, per) * std::max(1, nsm);
+  if (slot) slot->store(n, std::memory_order_relaxed);
+  return n;
+}
+
+// CTAs per tile: one wave over all tiles (at least one CTA per tile), at most
+// one CTA per `per_cta` work items of a tile, and at most kEigCtas in all
+// (the partial-sum scratch holds kEigCtas CTAs).
+static int ctas_per_tile(int wave, int tiles, long long items, int per_cta) {
+  const long long want = (items + per_cta - 1) / per_cta;
+  const int cap = std::max(1, std::min(wave, kEigCtas) / tiles);
+  return (int)std::max(1LL, std::min<long long>(cap, want));
+}
+
+// Item k = c cs + e (c = 0, 1, 2) of a native field: the 8 reals [8c, 8c + 8)
+// of element e, i.e. 4 complex numbers. FP32/FP64: the groups 2c and 2c + 1
+// of element e; FP16: chunk c of element e (one 16-byte load) times e's scale.
+template <class S, class U>
+__device__ __forceinline__ void ld8(const char *p, long long soff, long long k, long long cs,
+                                    U v[8]) {
+  const long long c = k / cs, e = k - c * cs;
+  if constexpr (std::is_same<S, F16>::value) {
+    float f[8];
+    unpack8<F16>(__ldg(reinterpret_cast<const uint4 *>(p) + k), f);
+    const float scl = __ldg(reinterpret_cast<const float *>(p + soff) + e);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (U)(f[q] * scl);
+  } else {
+    ld4<S>(p, 2 * c * cs + e, cs, v);
+    ld4<S>(p, (2 * c + 1) * cs + e, cs, v + 4);
+  }
+}
+template <class S, class U>
+__device__ __forceinline__ void st8(char *p, long long k, long long cs, const U v[8]) {
+  const long long c = k / cs, e = k - c * cs;
+  st4<S>(p, 2 * c * cs + e, cs, v);
+  st4<S>(p, (2 * c + 1) * cs + e, cs, v + 4);
+}
+
 // ---------------------------------------------------------------------------
 // Multi-dot: G[i][j] = <X_i, Y_j> over tiles of TI x TJ vector pairs.
 // ---------------------------------------------------------------------------
 struct GramArgs {
   const char *x = nullptr;
   long long xvs = 0;
+  long long xsoff = 0;  // FP16 X: byte offset of the scales within a vector
   int nx = 0;
   const char *y = nullptr;
   long long yvs = 0;
@@ -137,11 +196,13 @@ __global__ void __launch_bounds__(kEigThreads) gram_kernel(const GramArgs a) {
   if (threadIdx.x == 0) a.counters[tile] = 0u;
 }
 
-// Few Y vectors (ny <= NJ <= 4) against many X: the 8 warps of a CTA walk the
-// same 32-element stretch, warp w taking X vectors ibase + w + 8 t (t < NI) and
-// every Y vector, so each X vector is read once per launch and the Y vectors
-// once per tile of 8 NI X vectors (the other warps' Y loads hit L1).
-template <int NI, int NJ, class SY>
+// Few Y vectors (ny <= NJ <= 4) against many X (FP32, or FP16 with scales):
+// the 8 warps of a CTA walk the same stretch of 32 elements (groups of 4 reals
+// or 16-byte chunks of 8 reals), warp w taking X vectors
+// ibase + w + 8 t (t < NI) and every Y vector, so each X vector is read once
+// per launch and the Y vectors once per tile of 8 NI X vectors (the other
+// warps' Y loads hit L1).
+template <int NI, int NJ, class SX, class SY>
 __global__ void __launch_bounds__(kEigThreads) gram_skinny_kernel(const GramArgs a) {
   constexpr int NV = 8 * NI * NJ * 2;
   static_assert(NV <= kMaxValues, "too many partial sums per CTA");
@@ -149,27 +210,69 @@ __global__ void __launch_bounds__(kEigThreads) gram_skinny_kernel(const GramArgs
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tile = blockIdx.y, ibase = tile * 8 * NI;
   KahanF acc[NI][NJ][2];
-  // unrolled so that two elements' loads are in flight per warp
+  if constexpr (std::is_same<SX, F32>::value && NJ > 1) {
+    // FP32 X against several Y: groups of 4 reals, all Y of the group loaded
+    // up front (two groups' loads in flight per thread); measured faster than
+    // the chunk loop below for 4 Y, slower for one
 #pragma unroll 2
-  for (long long i = blockIdx.x * 32LL + lane; i < a.n4; i += gridDim.x * 32LL) {
-    float y[NJ][4];
+    for (long long i = blockIdx.x * 32LL + lane; i < a.n4; i += gridDim.x * 32LL) {
+      float y[NJ][4];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      if (j < a.ny)
-        ld4<SY>(a.y + j * a.yvs, i, a.cs, y[j]);
-      else
-        y[j][0] = y[j][1] = y[j][2] = y[j][3] = 0.f;
+      for (int j = 0; j < NJ; ++j) {
+        if (j < a.ny)
+          ld4<SY>(a.y + j * a.yvs, i, a.cs, y[j]);
+        else
+          y[j][0] = y[j][1] = y[j][2] = y[j][3] = 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < NI; ++t) {
+        const int xi = ibase + w + 8 * t;
+        if (xi < a.nx) {
+          float x[4];
+          ld4<F32>(a.x + xi * a.xvs, i, a.cs, x);
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            acc[t][j][0].add(x[0] * y[j][0] + x[1] * y[j][1] + x[2] * y[j][2] + x[3] * y[j][3]);
+            acc[t][j][1].add(x[0] * y[j][1] - x[1] * y[j][0] + x[2] * y[j][3] - x[3] * y[j][2]);
+          }
+        }
+      }
     }
+  } else {
+    // FP16 X, or FP32 X against one Y: 16-byte chunks of 8 reals (FP32: two
+    // groups; FP16: one chunk and its scale)
+    const long long n8 = 3 * a.cs;
+    for (long long k = blockIdx.x * 32LL + lane; k < n8; k += gridDim.x * 32LL) {
+      // this warp's X items first, then one Y item at a time (few registers:
+      // the Y loads of the 8 warps hit L1 after the first)
+      float x[NI][8];
 #pragma unroll
-    for (int t = 0; t < NI; ++t) {
-      const int xi = ibase + w + 8 * t;
-      if (xi < a.nx) {
-        float x[4];
-        ld4<F32>(a.x + xi * a.xvs, i, a.cs, x);
+      for (int t = 0; t < NI; ++t) {
+        const int xi = ibase + w + 8 * t;
+        if (xi < a.nx) {
+          ld8<SX>(a.x + xi * a.xvs, a.xsoff, k, a.cs, x[t]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          acc[t][j][0].add(x[0] * y[j][0] + x[1] * y[j][1] + x[2] * y[j][2] + x[3] * y[j][3]);
-          acc[t][j][1].add(x[0] * y[j][1] - x[1] * y[j][0] + x[2] * y[j][3] - x[3] * y[j][2]);
+          for (int q = 0; q < 8; ++q) x[t][q] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        if (j < a.ny) {
+          float y[8];
+          ld8<SY>(a.y + j * a.yvs, 0, k, a.cs, y);
+#pragma unroll
+          for (int t = 0; t < NI; ++t) {
+            // conj(x) y on the item's four complex numbers
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+              re += x[t][q] * y[q] + x[t][q + 1] * y[q + 1];
+              im += x[t][q] * y[q + 1] - x[t][q + 1] * y[q];
+            }
+            acc[t][j][0].add(re);
+            acc[t][j][1].add(im);
+          }
         }
       }
     }
@@ -210,41 +313,52 @@ __global__ void __launch_bounds__(kEigThreads) gram_skinny_kernel(const GramArgs
   if (threadIdx.x == 0) a.counters[tile] = 0u;
 }
 
-template <int NI, int NJ>
-static void gram_skinny_launch(const GramArgs &a, dwf_prec yprec, cudaStream_t st) {
+template <int NI, int NJ, class SX, class SY>
+static void gram_skinny_go(const GramArgs &a, cudaStream_t st) {
   const int tiles = (a.nx + 8 * NI - 1) / (8 * NI);
-  const long long want = (a.n4 + 31) / 32;
-  const int ctas = (int)std::max(1LL, std::min<long long>(std::max(1, kEigCtas / tiles), want));
-  dim3 grid(ctas, tiles);
-  if (yprec == DWF_FP64)
-    gram_skinny_kernel<NI, NJ, F64><<<grid, kEigThreads, 0, st>>>(a);
-  else
-    gram_skinny_kernel<NI, NJ, F32><<<grid, kEigThreads, 0, st>>>(a);
+  dim3 grid(ctas_per_tile(wave_ctas<gram_skinny_kernel<NI, NJ, SX, SY>>(), tiles, 3 * a.cs, 32),
+            tiles);
+  gram_skinny_kernel<NI, NJ, SX, SY><<<grid, kEigThreads, 0, st>>>(a);
   DWF_CUDA_TRY(cudaGetLastError());
+}
+template <int NI, int NJ>
+static void gram_skinny_launch(const GramArgs &a, dwf_prec xprec, dwf_prec yprec,
+                               cudaStream_t st) {
+  if (xprec == DWF_FP16)
+    yprec == DWF_FP64 ? gram_skinny_go<NI, NJ, F16, F64>(a, st)
+                      : gram_skinny_go<NI, NJ, F16, F32>(a, st);
+  else
+    yprec == DWF_FP64 ? gram_skinny_go<NI, NJ, F32, F64>(a, st)
+                      : gram_skinny_go<NI, NJ, F32, F32>(a, st);
 }
 
 template <int TI, int TJ>
 static void gram_launch(const GramArgs &a, dwf_prec yprec, cudaStream_t st) {
   const int tiles = ((a.nx + TI - 1) / TI) * ((a.ny + TJ - 1) / TJ);
-  long long want = (a.n4 + kEigThreads - 1) / kEigThreads;
-  const int ctas = (int)std::max(1LL, std::min<long long>(std::max(1, kEigCtas / tiles), want));
-  dim3 grid(ctas, tiles);
-  if (yprec == DWF_FP64)
+  if (yprec == DWF_FP64) {
+    dim3 grid(ctas_per_tile(wave_ctas<gram_kernel<TI, TJ, F64>>(), tiles, a.n4, kEigThreads),
+              tiles);
     gram_kernel<TI, TJ, F64><<<grid, kEigThreads, 0, st>>>(a);
-  else
+  } else {
+    dim3 grid(ctas_per_tile(wave_ctas<gram_kernel<TI, TJ, F32>>(), tiles, a.n4, kEigThreads),
+              tiles);
     gram_kernel<TI, TJ, F32><<<grid, kEigThreads, 0, st>>>(a);
+  }
   DWF_CUDA_TRY(cudaGetLastError());
 }
 
 void gram(const VecSet &X, const VecSet &Y, long long cs, double2 *G, int ldg,
           const DotScratch &w, cudaStream_t st) {
-  DWF_REQUIRE(X.prec == DWF_FP32 && (Y.prec == DWF_FP32 || Y.prec == DWF_FP64),
-              DWF_ERR_INVALID_ARG, "gram: X must be FP32, Y FP32 or FP64");
+  DWF_REQUIRE((X.prec == DWF_FP32 || (X.prec == DWF_FP16 && Y.n <= 4)) &&
+                  (Y.prec == DWF_FP32 || Y.prec == DWF_FP64),
+              DWF_ERR_INVALID_ARG,
+              "gram: X must be FP32 (or FP16 against at most 4 Y), Y FP32 or FP64");
   DWF_REQUIRE(X.n >= 1 && X.n <= kMaxEig && Y.n >= 1 && Y.n <= kMaxEig, DWF_ERR_INVALID_ARG,
               "gram: 1 .. 64 vectors per side");
   GramArgs a;
   a.x = X.p;
   a.xvs = X.vs;
+  a.xsoff = X.soff;
   a.nx = X.n;
   a.y = Y.p;
   a.yvs = Y.vs;
@@ -256,11 +370,11 @@ void gram(const VecSet &X, const VecSet &Y, long long cs, double2 *G, int ldg,
   a.partials = w.partials;
   a.counters = w.counters;
   if (Y.n == 1)
-    gram_skinny_launch<2, 1>(a, Y.prec, st);
+    gram_skinny_launch<2, 1>(a, X.prec, Y.prec, st);
   else if (Y.n == 2)
-    gram_skinny_launch<2, 2>(a, Y.prec, st);
+    gram_skinny_launch<2, 2>(a, X.prec, Y.prec, st);
   else if (Y.n <= 4)
-    gram_skinny_launch<2, 4>(a, Y.prec, st);
+    gram_skinny_launch<2, 4>(a, X.prec, Y.prec, st);
   else
     gram_launch<4, 4>(a, Y.prec, st);
 }
@@ -271,6 +385,7 @@ void gram(const VecSet &X, const VecSet &Y, long long cs, double2 *G, int ldg,
 struct CombineArgs {
   const char *x = nullptr;
   long long xvs = 0;
+  long long xsoff = 0;  // FP16 X: byte offset of the scales within a vector
   int nx = 0;
   const double2 *C = nullptr;
   int ldc = 0;
@@ -283,7 +398,9 @@ struct CombineArgs {
   long long n4 = 0, cs = 0;
 };
 
-template <int TJ, class SO>
+// One item (8 reals) of every output per thread and grid-stride step; X is
+// FP32 or FP16 with scales, the outputs FP32 or FP64.
+template <int TJ, class SX, class SO>
 __global__ void __launch_bounds__(kEigThreads) combine_kernel(const CombineArgs a) {
   using R = typename std::conditional<std::is_same<SO, F64>::value, double, float>::type;
   __shared__ R cr[kMaxEig][TJ], ci[kMaxEig][TJ];
@@ -306,56 +423,70 @@ __global__ void __launch_bounds__(kEigThreads) combine_kernel(const CombineArgs 
 #pragma unroll
   for (int j = 0; j < TJ; ++j)
     live[j] = j0 + j < a.nout && !(a.skip && a.skip[j0 + j]);
-  FLAT_LOOP(a.n4) {
-    R acc[TJ][4];
+  const long long n8 = 3 * a.cs;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n8;
+       k += (long long)gridDim.x * blockDim.x) {
+    R acc[TJ][8];
 #pragma unroll
     for (int j = 0; j < TJ; ++j) {
-      if (a.base && live[j])
-        ld4<SO>(a.base + (j0 + j) * a.ovs, i, a.cs, acc[j]);
-      else
-        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = (R)0;
+      if (a.base && live[j]) {
+        ld8<SO>(a.base + (j0 + j) * a.ovs, 0, k, a.cs, acc[j]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[j][q] = (R)0;
+      }
     }
     for (int t = 0; t < a.nx; ++t) {
-      float x[4];
-      ld4<F32>(a.x + t * a.xvs, i, a.cs, x);
+      float x[8];
+      ld8<SX>(a.x + t * a.xvs, a.xsoff, k, a.cs, x);
 #pragma unroll
       for (int j = 0; j < TJ; ++j) {
         const R r = cr[t][j], m = ci[t][j];
-        acc[j][0] += (R)x[0] * r - (R)x[1] * m;
-        acc[j][1] += (R)x[0] * m + (R)x[1] * r;
-        acc[j][2] += (R)x[2] * r - (R)x[3] * m;
-        acc[j][3] += (R)x[2] * m + (R)x[3] * r;
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          acc[j][q] += (R)x[q] * r - (R)x[q + 1] * m;
+          acc[j][q + 1] += (R)x[q] * m + (R)x[q + 1] * r;
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < TJ; ++j)
-      if (live[j]) st4<SO>(a.out + (j0 + j) * a.ovs, i, a.cs, acc[j]);
+      if (live[j]) st8<SO>(a.out + (j0 + j) * a.ovs, k, a.cs, acc[j]);
   }
 }
 
-template <int TJ>
-static void combine_launch(const CombineArgs &a, dwf_prec oprec, cudaStream_t st) {
+template <int TJ, class SX, class SO>
+static void combine_go(const CombineArgs &a, cudaStream_t st) {
   const int tiles = (a.nout + TJ - 1) / TJ;
-  long long want = (a.n4 + kEigThreads - 1) / kEigThreads;
-  const int ctas = (int)std::max(1LL, std::min<long long>(std::max(1, 2 * kEigCtas / tiles), want));
-  dim3 grid(ctas, tiles);
-  if (oprec == DWF_FP64)
-    combine_kernel<TJ, F64><<<grid, kEigThreads, 0, st>>>(a);
-  else
-    combine_kernel<TJ, F32><<<grid, kEigThreads, 0, st>>>(a);
+  dim3 grid(ctas_per_tile(wave_ctas<combine_kernel<TJ, SX, SO>>(), tiles, 3 * a.cs, kEigThreads),
+            tiles);
+  combine_kernel<TJ, SX, SO><<<grid, kEigThreads, 0, st>>>(a);
   DWF_CUDA_TRY(cudaGetLastError());
+}
+// FP64 outputs take at most 4 per tile (8 doubles of accumulators each).
+template <int TJ>
+static void combine_launch(const CombineArgs &a, dwf_prec xprec, dwf_prec oprec,
+                           cudaStream_t st) {
+  if (oprec == DWF_FP64) {
+    constexpr int T = TJ > 4 ? 4 : TJ;
+    xprec == DWF_FP16 ? combine_go<T, F16, F64>(a, st) : combine_go<T, F32, F64>(a, st);
+  } else {
+    xprec == DWF_FP16 ? combine_go<TJ, F16, F32>(a, st) : combine_go<TJ, F32, F32>(a, st);
+  }
 }
 
 void combine(const VecSet &X, const double2 *C, int ldc, const double *wi, const char *base,
              char *out, long long ovs, dwf_prec oprec, int nout, const int *skip, long long cs,
              cudaStream_t st) {
-  DWF_REQUIRE(X.prec == DWF_FP32 && (oprec == DWF_FP32 || oprec == DWF_FP64),
-              DWF_ERR_INVALID_ARG, "combine: X must be FP32, the output FP32 or FP64");
+  DWF_REQUIRE((X.prec == DWF_FP32 || X.prec == DWF_FP16) &&
+                  (oprec == DWF_FP32 || oprec == DWF_FP64),
+              DWF_ERR_INVALID_ARG, "combine: X must be FP32 or FP16, the output FP32 or FP64");
   DWF_REQUIRE(X.n >= 1 && X.n <= kMaxEig && nout >= 1 && nout <= kMaxEig, DWF_ERR_INVALID_ARG,
               "combine: 1 .. 64 vectors per side");
   CombineArgs a;
   a.x = X.p;
   a.xvs = X.vs;
+  a.xsoff = X.soff;
   a.nx = X.n;
   a.C = C;
   a.ldc = ldc;
@@ -368,13 +499,13 @@ void combine(const VecSet &X, const double2 *C, int ldc, const double *wi, const
   a.n4 = 6 * cs;
   a.cs = cs;
   if (nout == 1)
-    combine_launch<1>(a, oprec, st);
+    combine_launch<1>(a, X.prec, oprec, st);
   else if (nout == 2)
-    combine_launch<2>(a, oprec, st);
+    combine_launch<2>(a, X.prec, oprec, st);
   else if (nout <= 4)
-    combine_launch<4>(a, oprec, st);
+    combine_launch<4>(a, X.prec, oprec, st);
   else
-    combine_launch<8>(a, oprec, st);
+    combine_launch<8>(a, X.prec, oprec, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -422,9 +553,8 @@ static void cheb_step(const char *ay, const char *y, const char *yprev, char *ou
   a.s1 = (float)s1;
   a.c = (float)c;
   a.s2 = (float)s2;
-  const int ctas = (int)std::min<long long>(std::max(1, 2 * kEigCtas / nvec),
-                                            (n4 + kEigThreads - 1) / kEigThreads);
-  cheb_kernel<<<dim3(std::max(1, ctas), nvec), kEigThreads, 0, st>>>(a);
+  const int ctas = ctas_per_tile(wave_ctas<cheb_kernel>(), nvec, n4, kEigThreads);
+  cheb_kernel<<<dim3(ctas, nvec), kEigThreads, 0, st>>>(a);
   DWF_CUDA_TRY(cudaGetLastError());
 }
 
@@ -904,6 +1034,8 @@ void deflate_start(const Deflation &d, const char *b64, char *x64, long long str
   Vs.p = d.V;
   Vs.vs = d.vs;
   Vs.n = d.n_ev;
+  Vs.prec = d.vprec;
+  Vs.soff = d.vsoff;
   VecSet Bs;
   Bs.p = b64;
   Bs.vs = stride64;
@@ -933,6 +1065,8 @@ void deflate_correct(const Deflation &d, dwf_prec lo, const char *r, char *z, lo
   Vs.p = d.V;
   Vs.vs = d.vs;
   Vs.n = d.n_ev;
+  Vs.prec = d.vprec;
+  Vs.soff = d.vsoff;
   VecSet Rs;
   Rs.p = r;
   Rs.vs = stride;

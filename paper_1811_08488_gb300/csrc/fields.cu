@@ -163,6 +163,59 @@ void launch_export(dwf_prec p, void *canon, int canon_fp32, const char *native, 
   DWF_CUDA_TRY(cudaGetLastError());
 }
 
+// Native -> native in another precision (FP16/BF16 outputs take the per-element
+// scale of the stored values).
+template <class SI, class SO>
+__global__ void convert_kernel(char *out, long long ostride, long long osoff, const char *in,
+                               long long istride, long long isoff, int n) {
+  const int rhs = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    typename SI::R v[24];
+    load24<SI>(in + rhs * istride, isoff, n, i, v);
+    typename SO::R w[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) w[k] = (typename SO::R)v[k];
+    store24<SO>(out + rhs * ostride, osoff, n, i, w);
+  }
+}
+
+template <class SI>
+static void convert_from(dwf_prec po, char *out, long long ostride, long long osoff,
+                         const char *in, long long istride, long long isoff, int n, int nrhs,
+                         cudaStream_t st) {
+  dim3 grid(1024, nrhs), block(256);
+  switch (po) {
+    case DWF_FP64:
+      convert_kernel<SI, F64><<<grid, block, 0, st>>>(out, ostride, osoff, in, istride, isoff, n);
+      break;
+    case DWF_FP32:
+      convert_kernel<SI, F32><<<grid, block, 0, st>>>(out, ostride, osoff, in, istride, isoff, n);
+      break;
+    case DWF_FP16:
+      convert_kernel<SI, F16><<<grid, block, 0, st>>>(out, ostride, osoff, in, istride, isoff, n);
+      break;
+    case DWF_BF16:
+      convert_kernel<SI, BF16><<<grid, block, 0, st>>>(out, ostride, osoff, in, istride, isoff, n);
+      break;
+  }
+}
+
+void launch_convert(dwf_prec po, char *out, dwf_prec pi, const char *in, int nsite, int Ls,
+                    int nrhs, cudaStream_t st) {
+  const long long ostride = (long long)field_rhs_bytes(po, nsite, Ls);
+  const long long istride = (long long)field_rhs_bytes(pi, nsite, Ls);
+  const long long osoff = (long long)align_up(field_data_bytes(po, nsite, Ls), 256);
+  const long long isoff = (long long)align_up(field_data_bytes(pi, nsite, Ls), 256);
+  const int n = nsite * Ls;
+  switch (pi) {
+    case DWF_FP64: convert_from<F64>(po, out, ostride, osoff, in, istride, isoff, n, nrhs, st); break;
+    case DWF_FP32: convert_from<F32>(po, out, ostride, osoff, in, istride, isoff, n, nrhs, st); break;
+    case DWF_FP16: convert_from<F16>(po, out, ostride, osoff, in, istride, isoff, n, nrhs, st); break;
+    case DWF_BF16: convert_from<BF16>(po, out, ostride, osoff, in, istride, isoff, n, nrhs, st); break;
+  }
+  DWF_CUDA_TRY(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // Gauge links. Input U[t][z][y][x][mu][3][3] complex128. Each link record
 // (owner, mu) -- owner = parity * Vh + idx/2, the combined numbering -- is cut

@@ -838,8 +838,12 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
                   "deflation: every lambda must be positive and finite");
       inv[j] = 1.0 / dfin->lambda[j];
     }
+    DWF_REQUIRE(dfin->vprec == DWF_FP32 || dfin->vprec == DWF_FP16, DWF_ERR_INVALID_ARG,
+                "deflation: V must be FP32 or FP16");
     defl.V = dfin->V;
-    defl.vs = (long long)field_rhs_bytes(DWF_FP32, Vh, Ls);
+    defl.vprec = dfin->vprec;
+    defl.vs = (long long)field_rhs_bytes(dfin->vprec, Vh, Ls);
+    defl.vsoff = (long long)align_up(field_data_bytes(dfin->vprec, Vh, Ls), 256);
     defl.n_ev = dfin->n_ev;
     defl.coarse = coarse ? 1 : 0;
     defl.c = sp->defl.as<double2>();
@@ -931,6 +935,7 @@ dwf_status solve(dwf_ctx *ctx, void *x, const void *b, int nrhs, const double *m
     key << (void *)bp << "/" << (bp ? bp->r.p : nullptr) << "/" << prm->inner_iters << "/"
         << prm->snake << "/" << plain << "/" << A.flexible << "/" << ctx->prof_on << "/"
         << (S.defl ? (const void *)S.defl->V : nullptr) << "/" << (S.defl ? S.defl->n_ev : 0)
+        << "/" << (S.defl ? (int)S.defl->vprec : -1)
         << "/" << coarse;
     for (int r = 0; r < nrhs; ++r) key << "/" << mf[r];
     if (!sp->loop || sp->loop_key != key.str()) {

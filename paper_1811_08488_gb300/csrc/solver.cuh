@@ -105,6 +105,7 @@ struct SolverPlan {
 // the coarse correction of the preconditioner.
 struct DeflationInput {
   const char *V = nullptr;
+  dwf_prec vprec = DWF_FP32;       // FP32 or FP16 (with scales)
   const double *lambda = nullptr;  // host [n_ev]
   int n_ev = 0;
   int coarse = 0;

@@ -34,7 +34,8 @@ EXPORTS = ["dwf_create", "dwf_destroy", "dwf_last_error", "dwf_solver_params_def
            "dwf_block_precond", "dwf_autotune_block", "dwf_source_prep", "dwf_odd_reconstruct",
            "dwf_mpc_sym", "dwf_mdagm_sym", "dwf_source_prep_sym",
            "mspcg_solve", "dwf_profile_enable", "dwf_profile_read",
-           "dwf_eig_params_default", "dwf_eig_lowmodes", "dwf_deflate", "mspcg_solve_deflated"]
+           "dwf_eig_params_default", "dwf_eig_lowmodes", "dwf_deflate", "mspcg_solve_deflated",
+           "dwf_field_convert"]
 
 
 class DwfError(RuntimeError):
@@ -123,9 +124,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dwf_eig_params_default": (None, [C.POINTER(EigParams)]),
         "dwf_eig_lowmodes": (I, [P, P, I, C.c_double, C.POINTER(EigParams), D, D,
                                  C.POINTER(EigInfo), P]),
-        "dwf_deflate": (I, [P, P, P, P, D, I, I, I, I, P]),
-        "mspcg_solve_deflated": (I, [P, P, P, I, D, C.POINTER(SolverParams), P, D, I, I,
+        "dwf_deflate": (I, [P, P, P, P, I, D, I, I, I, I, P]),
+        "mspcg_solve_deflated": (I, [P, P, P, I, D, C.POINTER(SolverParams), P, I, D, I, I,
                                      C.POINTER(SolveInfo), P]),
+        "dwf_field_convert": (I, [P, P, I, P, I, I, P]),
         "dwf_profile_read": (I, [P, C.POINTER(KernelTime), I, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -418,16 +420,23 @@ class Context:
                                            C.byref(info), _stream(stream)))
         return theta, resid, info.as_dict()
 
-    def deflate(self, z, r, V, lam, prec, nrhs=1, accumulate=False, stream=None):
+    def field_convert(self, out, out_prec, inp, in_prec, nrhs=1, stream=None):
+        """dwf_field_convert: native fields from in_prec to out_prec."""
+        self._check(lib().dwf_field_convert(self._h, C.c_void_p(_ptr(out)),
+                                            PREC.get(out_prec, out_prec), C.c_void_p(_ptr(inp)),
+                                            PREC.get(in_prec, in_prec), int(nrhs),
+                                            _stream(stream)))
+
+    def deflate(self, z, r, V, lam, prec, nrhs=1, accumulate=False, vprec="fp32", stream=None):
         """dwf_deflate: z = (z if accumulate) + V Lambda^-1 V^+ r."""
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         self._check(lib().dwf_deflate(self._h, C.c_void_p(_ptr(z)), C.c_void_p(_ptr(r)),
-                                      C.c_void_p(_ptr(V)),
+                                      C.c_void_p(_ptr(V)), PREC.get(vprec, vprec),
                                       lam.ctypes.data_as(C.POINTER(C.c_double)), lam.size,
                                       PREC.get(prec, prec), int(nrhs), int(bool(accumulate)),
                                       _stream(stream)))
 
-    def solve_deflated(self, x, b, mf, params, V, lam, coarse=True, stream=None,
+    def solve_deflated(self, x, b, mf, params, V, lam, coarse=True, vprec="fp32", stream=None,
                        raise_on_error=True):
         """mspcg_solve_deflated with the Ritz pairs (V, lam). Returns (status,
         [info dict per rhs])."""
@@ -438,6 +447,7 @@ class Context:
         bp = b.ctypes.data if isinstance(b, np.ndarray) else _ptr(b)
         st = lib().mspcg_solve_deflated(self._h, C.c_void_p(xp), C.c_void_p(bp), m.size, mp,
                                         C.byref(params), C.c_void_p(_ptr(V)),
+                                        PREC.get(vprec, vprec),
                                         lam.ctypes.data_as(C.POINTER(C.c_double)), lam.size,
                                         int(bool(coarse)), infos, _stream(stream))
         if st != 0 and raise_on_error and st != 4:

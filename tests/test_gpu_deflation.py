@@ -2,9 +2,10 @@
 
 * dwf_deflate (z = V Lambda^-1 V^+ r, the kernels of the deflated start and
   of the coarse correction) element by element against the oracle's
-  coarse_correction, for FP32 and FP64 fields, 1 to 3 right-hand sides (the
-  three tile shapes of the multi-dot kernel) and 1 to 33 vectors (ragged
-  tiles), and at the 16^3x32 x Ls=12 size;
+  coarse_correction, for FP32 and FP64 fields, 1 to 4 right-hand sides (the
+  tile shapes of the multi-dot kernel) and 1 to 33 vectors (ragged tiles),
+  with V in FP32 and in FP16, and at the 16^3x32 x Ls=12 size;
+* dwf_field_convert between FP32, FP64 and FP16;
 * dwf_eig_lowmodes against numpy's eigh of the oracle's dense A on a
   4x2x2x4 x Ls=4 lattice: Ritz values, the invariant subspace and the
   orthonormality of the Ritz vectors;
@@ -102,6 +103,56 @@ def test_deflate_matches_oracle(prec, tol, n_ev, nrhs, accumulate):
         assert relerr(got[k], want) < tol, (k, relerr(got[k], want))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n_ev,nrhs", [(1, 1), (17, 2), (24, 4)])
+def test_deflate_fp16_vectors_match_oracle(prec, n_ev, nrhs):
+    """V stored in FP16 with per-(site, s) scales (dwf_field_convert from FP32):
+    every element of V carries a relative rounding of at most 2^-11 of its
+    (site, s) maximum, so the projection and the combination are within about
+    3 * 2^-11 of the FP64 result (tolerance 2e-3)."""
+    dims, Ls = (4, 4, 2, 6), 4
+    act, U, ctx = setup(dims, Ls, 302)
+    V = [syn.half_field(dims, Ls, 410 + j) for j in range(n_ev)]
+    lam = np.linspace(0.05, 2.0, n_ev)
+    r = [syn.half_field(dims, Ls, 510 + k) for k in range(nrhs)]
+    V32 = to_native_many(ctx, V, "fp32")
+    V16 = ctx.new_field("fp16", n_ev)
+    ctx.field_convert(V16, "fp16", V32, "fp32", n_ev)
+    rn = to_native(ctx, r, prec)
+    zn = ctx.new_field(prec, nrhs)
+    ctx.deflate(zn, rn, V16, lam, prec, nrhs, vprec="fp16")
+    got = from_native_many(ctx, zn, prec, nrhs)
+    for k in range(nrhs):
+        want = df.coarse_correction(V, lam, r[k])
+        assert relerr(got[k], want) < 2e-3, (k, relerr(got[k], want))
+
+
+def test_field_convert_round_trips():
+    """FP32 -> FP64 -> FP32 is exact; FP32 -> FP16 keeps every element within
+    2^-11 of its (site, s) maximum; FP16 -> FP32 -> FP16 is exact."""
+    dims, Ls = (4, 4, 2, 6), 6
+    ctx = dwf().Context(dims, Ls, **MOB)
+    halves = [syn.half_field(dims, Ls, 520 + k) for k in range(3)]
+    f32 = to_native(ctx, halves, "fp32")
+    f64, back = ctx.new_field("fp64", 3), ctx.new_field("fp32", 3)
+    ctx.field_convert(f64, "fp64", f32, "fp32", 3)
+    ctx.field_convert(back, "fp32", f64, "fp64", 3)
+    torch.cuda.synchronize()
+    assert torch.equal(back, f32)
+    f16, b32, b16 = ctx.new_field("fp16", 3), ctx.new_field("fp32", 3), ctx.new_field("fp16", 3)
+    ctx.field_convert(f16, "fp16", f32, "fp32", 3)
+    ctx.field_convert(b32, "fp32", f16, "fp16", 3)
+    ctx.field_convert(b16, "fp16", b32, "fp32", 3)
+    torch.cuda.synchronize()
+    assert torch.equal(b16, f16)
+    got = from_native_many(ctx, f16, "fp16", 3)
+    for k in range(3):
+        g = np.stack([got[k].real, got[k].imag], -1)
+        w = np.stack([halves[k].real, halves[k].imag], -1)
+        elem_max = np.abs(w).max(axis=(-3, -2, -1), keepdims=True)
+        assert (np.abs(g - w) / elem_max).max() <= 2.0 ** -11 * 1.01
+
+
 def test_deflate_full_size_16x16x16x32():
     """dwf_deflate on the 16^3x32 x Ls=12 lattice (8 vectors, 2 right-hand
     sides), every element against the oracle."""
@@ -180,10 +231,14 @@ def test_eig_lowmodes_rejects_bad_arguments():
         ctx.eig_lowmodes(Vn, 65, 0.02, d.default_eig_params(n_ev=4))  # m > 64
     with pytest.raises(d.DwfError):
         ctx.deflate(ctx.new_field("fp32", 1), ctx.new_field("fp32", 1), Vn, [1.0, -1.0], "fp32")
+    with pytest.raises(d.DwfError) as e:  # FP16 V with more than 4 right-hand sides
+        ctx.deflate(ctx.new_field("fp32", 5), ctx.new_field("fp32", 5), Vn, [1.0], "fp32", 5,
+                    vprec="fp16")
+    assert e.value.code == 2
 
 
-@pytest.mark.parametrize("k", [0, 3])
-def test_deflated_solve_fewer_iterations(k):
+@pytest.mark.parametrize("k,vprec", [(0, "fp32"), (3, "fp32"), (3, "fp16")])
+def test_deflated_solve_fewer_iterations(k, vprec):
     """Low modes from dwf_eig_lowmodes; the deflated solve (start and coarse
     correction) converges with the oracle's recomputed residual <= 1e-10 and
     needs fewer outer iterations than the same solve without deflation."""
@@ -200,11 +255,15 @@ def test_deflated_solve_fewer_iterations(k):
     prm = dwf().default_params(block=(4, 4, 4, 4), inner_iters=k, inner="fp16", tol=1e-10)
     x0 = torch.zeros_like(bt)
     st, info0 = ctx.solve(x0, bt, [mf], prm)
-    rs = ctx.field_bytes("fp32", 1)
+    rs = ctx.field_bytes(vprec, 1)
+    if vprec == "fp16":
+        V16 = ctx.new_field("fp16", n_ev)
+        ctx.field_convert(V16, "fp16", Vn, "fp32", n_ev)
+        Vn = V16
     for coarse in (0, 1):
         x = torch.zeros_like(bt)
         st, info1 = ctx.solve_deflated(x, bt, [mf], prm, Vn[:n_ev * rs], theta[:n_ev],
-                                       coarse=coarse)
+                                       coarse=coarse, vprec=vprec)
         assert st == 0 and info1[0]["converged"] == 1
         xf = op.half_to_full(x.cpu().numpy()[0], 0)
         bf = op.half_to_full(b, 0)
