@@ -443,7 +443,8 @@ dwf_status dwf_eig_lowmodes(dwf_ctx *ctx, void *V, int m, double mf, const dwf_e
  * vprec, 1) bytes apart), 1 <= n_ev <= DWF_MAX_EIG, orthonormal; lambda: host
  * array of n_ev positive values; z, r: native fields of precision prec
  * (DWF_FP32 or DWF_FP64) that do not alias. FP16 V serves at most 4
- * right-hand sides per call.
+ * right-hand sides per call. Synchronous (lambda is copied to the device on
+ * `stream` and the call waits for the stream before it returns).
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 dwf_status dwf_deflate(dwf_ctx *ctx, void *z, const void *r, const void *V, dwf_prec vprec,
                        const double *lambda, int n_ev, dwf_prec prec, int nrhs, int accumulate,
