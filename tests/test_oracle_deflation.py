@@ -193,3 +193,23 @@ def test_pcg_with_initial_guess_matches_zero_start_on_exact_guess(brute):
     x1, it1, _ = sv.pcg(A, lambda v: v, b, 1e-10, x0=np.zeros_like(b))
     x2, it2, _ = sv.pcg(A, lambda v: v, b, 1e-10)
     assert it1 == it2 and np.abs(x1 - x2).max() == 0
+
+
+def test_lowmodes_of_the_symmetric_form_match_dense_eigh(brute):
+    """The same subspace iteration on A_sym = D_sym^dag D_sym (the symmetric
+    Schur form's normal operator) against numpy's eigh of its dense matrix."""
+    act, U, mf, _, _, idx, _, _ = brute
+    A = lambda v: op.mdagm_sym(act, U, v, mf)
+    Ad, _ = dense_even(act, A)
+    w, Q = np.linalg.eigh(0.5 * (Ad + Ad.conj().T))
+    gaps = np.diff(w[:16]) / w[:16][1:]
+    n_ev = int(np.argmax(gaps[5:12])) + 6
+    m = n_ev + 6
+    V0 = [even_random(act, 300 + j) for j in range(m)]
+    lam_max = df.lambda_max_estimate(A, V0[0])
+    theta, V, res, passes = df.lowmodes(A, V0, n_ev, degree=16, passes=80, lam_max=lam_max,
+                                        tol=1e-11)
+    assert passes < 80
+    assert np.abs(theta[:n_ev] - w[:n_ev]).max() < 1e-9 * w.max()
+    Vm = np.stack([from_field(idx, v) for v in V[:n_ev]], axis=1)
+    assert projector_distance(Vm, Q[:, :n_ev]) < 1e-6
